@@ -1,0 +1,192 @@
+/*
+ * svt_gb300.h -- C ABI of the GB300 (sm_103a) implementation of fast singular value
+ * thresholding with the recycling rank-revealing randomized SVD (Li & Yu,
+ * "A Fast Implementation of Singular Value Thresholding Algorithm using Recycling
+ * Rank Revealing Randomized Singular Value Decomposition").
+ *
+ * Problem (eq. (1)-(3)): complete an m x n matrix A from the entries observed on the
+ * index set Lambda.  The solver runs the Uzawa / linearized-Bregman iteration of
+ * eq. (4), X = D_tau(Y), Y <- Y + delta P_Lambda(A - X), with the shrinkage operator
+ * D_tau of eq. (5) evaluated through R4SVD (Algorithm 3; Algorithm 2 on the first
+ * iteration) and the cooled precision threshold of Section 2.5 (Algorithm 4).
+ *
+ * Conventions shared by every entry point
+ *  - Indices are 0-based int32; nnz < 2^31.  Lambda is a set: duplicate (row, col)
+ *    pairs and out-of-range indices are errors.
+ *  - Dense matrices are row-major: element (i, j) of an R x C matrix with leading
+ *    dimension ld lives at p[i * ld + j], ld >= C.
+ *  - Values observed on Lambda are kept in CSR order (sorted by row, then column);
+ *    a vector "in CSR order" has one entry per observed position in that order.
+ *  - Precision SVT_FP64 computes everything in binary64.  SVT_MIXED_FP32 keeps the
+ *    observed values, Y and the tall-skinny blocks in binary32 and computes the
+ *    Gram matrices, Cholesky factors, the small eigenproblem and all norms and
+ *    threshold decisions in binary64 (or binary64-accurate arithmetic).
+ *  - Work is queued on `stream` (a cudaStream_t; NULL is the legacy default stream).
+ *    Every call returns after the work it queued has finished.
+ *  - A call that fails returns a negative svt_status; svt_last_error() then gives a
+ *    message for the calling thread.  No entry point terminates the process, and
+ *    none leaves work running on the GPU when it returns.
+ *  - The library allocates its own device scratch memory (stream-ordered); inputs
+ *    and outputs are owned by the caller.
+ */
+#ifndef SVT_GB300_H
+#define SVT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum svt_status {
+  SVT_OK = 0,              /* converged (residual < tol) or the call finished      */
+  SVT_NOT_CONVERGED = 1,   /* maxit iterations done; the last iterate is returned   */
+  SVT_ERR_ARG = -1,        /* invalid argument (sizes, parameters, capacities)      */
+  SVT_ERR_INDEX = -2,      /* an observed index lies outside [0,m) x [0,n)          */
+  SVT_ERR_DUPLICATE = -3,  /* an observed (row, col) pair occurs twice              */
+  SVT_ERR_CUDA = -4,       /* a CUDA runtime call failed                            */
+  SVT_ERR_NUMERIC = -6,    /* non-finite input value, or a non-finite iterate       */
+  SVT_ERR_UNSUPPORTED = -8 /* size beyond what this build supports                  */
+} svt_status;
+
+typedef enum svt_precision {
+  SVT_FP64 = 0,
+  SVT_MIXED_FP32 = 1
+} svt_precision;
+
+/* Solver options.  Defaults (svt_default_options) follow Section 3: t =
+ * floor(0.05 min(m,n)), dt = 10, beta = 0.95; no power iterations. */
+typedef struct svt_options {
+  int32_t t;            /* width of the first Gaussian block; <= 0: floor(0.05 min(m,n)), at least 1 */
+  int32_t dt;           /* width of each further block (Algorithms 2-3: Delta t)        */
+  int32_t n_power;      /* power iterations X <- Y (Y^T X) per block (np)              */
+  int32_t r_max;        /* rank cap; r <= min(m, n, r_max); <= 0: min(m, n)            */
+  int32_t power_steps;  /* power steps for ||P_Lambda(A)||_2 in the initialisation     */
+  int32_t precision;    /* svt_precision                                               */
+  double beta;          /* cooling factor for the precision threshold (0 < beta < 1)   */
+  double eps_thr0;      /* initial error-percentage threshold                          */
+  uint64_t seed;        /* key of the counter-based Gaussian generator                 */
+  void* stream;         /* cudaStream_t                                                */
+} svt_options;
+
+/* Per-iteration record (the analogue of the paper's per-iteration timing plots). */
+typedef struct svt_iter_log {
+  int32_t iter;         /* SVT iteration i (1-based)                                   */
+  int32_t r;            /* revealed rank of R4SVD                                      */
+  int32_t k;            /* singular values above tau (rank of X^(i))                   */
+  int32_t blocks;       /* Gaussian blocks drawn in this iteration                     */
+  int32_t cooled;       /* 1 if the threshold was multiplied by beta after this step   */
+  int32_t exhausted;    /* 1 if a block found the range of Y exhausted                 */
+  double eps;           /* final error percentage of the QB decomposition              */
+  double eps_thr;       /* threshold used in this iteration                            */
+  double rel_residual;  /* ||P_Lambda(A - X^(i))||_F / ||P_Lambda(A)||_F               */
+  double mae;           /* mean |A - X^(i)| over the observed entries                  */
+  double sigma_max;     /* largest singular value of Y^(i)                             */
+  double seconds;       /* wall time of the iteration (host clock, after its sync)     */
+} svt_iter_log;
+
+typedef struct svt_result {
+  int32_t status;       /* svt_status of the call                                      */
+  int32_t iters;        /* iterations run                                              */
+  int32_t k;            /* rank of the returned X                                      */
+  int32_t r;            /* last revealed rank                                          */
+  int32_t k0;           /* kick-start multiple of the initialisation                   */
+  int32_t log_len;      /* entries written to the log buffer                           */
+  double rel_residual;  /* residual of the returned X                                  */
+  double mae;
+  double spec_norm;     /* ||P_Lambda(A)||_2 estimate used by the initialisation       */
+  double eps_thr;       /* threshold at exit                                           */
+  double seconds_pattern; /* time spent building the sorted pattern                    */
+  double seconds_total;
+} svt_result;
+
+typedef struct svt_pattern svt_pattern;   /* opaque: the observed set on the device */
+
+/* ------------------------------------------------------------------ utilities */
+int svt_abi_version(void);
+void svt_default_options(svt_options* opt);
+const char* svt_status_string(int status);
+/* Message describing the last failure on the calling thread (never NULL). */
+const char* svt_last_error(void);
+
+/* ------------------------------------------------------------------ pattern */
+/* Build the observed set Lambda (P_Lambda of eq. (4)) from device COO arrays rows[nnz],
+ * cols[nnz].  Sorts into CSR (row, col) and CSC (col, row) orders with a stable radix
+ * sort; rejects out-of-range indices (SVT_ERR_INDEX) and duplicates
+ * (SVT_ERR_DUPLICATE).  *out receives a handle owned by the caller. */
+svt_status svt_pattern_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                              const int32_t* cols, void* stream, svt_pattern** out);
+void svt_pattern_destroy(svt_pattern* p);
+int64_t svt_pattern_nnz(const svt_pattern* p);
+/* Copy the sorted pattern into caller device buffers (any may be NULL):
+ * row_ptr[m+1], col_idx[nnz] (CSR), csr_src[nnz] (input position of each CSR slot),
+ * col_ptr[n+1], row_idx[nnz] (CSC), perm[nnz] (CSR slot of each CSC slot). */
+svt_status svt_pattern_export(const svt_pattern* p, int32_t* row_ptr, int32_t* col_idx,
+                              int32_t* csr_src, int32_t* col_ptr, int32_t* row_idx,
+                              int32_t* perm, void* stream);
+
+/* ------------------------------------------------------------------ building blocks */
+/* Gaussian test block Omega (Algorithms 2-3): n x w standard normals, binary64,
+ * row-major with leading dimension ld, device memory.  Entry (j, c) comes from
+ * Philox4x32-10 (Salmon et al., SC'11) with counter (j, c/2, iter, block) and key
+ * (seed low 32 bits, seed high 32 bits), turned into normals by Box-Muller. */
+svt_status svt_gaussian_block(uint64_t seed, uint32_t iter, uint32_t block, int64_t n,
+                              int32_t w, double* out, int64_t ld, void* stream);
+
+/* Sparse times tall-skinny block with Y supported on Lambda (the matrix-block
+ * products of Algorithms 1-3).  y_csr: values in CSR order (double for SVT_FP64,
+ * float for SVT_MIXED_FP32).  transpose = 0: out (m x w) = Y W with W n x w;
+ * transpose = 1: out (n x w) = Y^T W with W m x w.  W and out have the element type
+ * of y_csr; all pointers are device pointers. */
+svt_status svt_spmm(const svt_pattern* p, int precision, int transpose, const void* y_csr,
+                    const void* W, int64_t ldw, int32_t w, void* out, int64_t ldo,
+                    void* stream);
+
+/* One sampled shrinkage-and-update pass (eq. (4)-(5) restricted to Lambda): for each
+ * observed (p, q) in CSR order, x = sum_{j<k} U[p, j] * W[q, j], d = a - x,
+ * y += delta * d.  U (m x k, ldu) and W (n x k, ldw) hold X^(i) = U W^T.  sums[0..2]
+ * (host memory) receive sum d^2, sum |d| and sum y_new^2 (binary64).  Element type
+ * of a_csr, y_csr, U and W as in svt_spmm. */
+svt_status svt_sampled_update(const svt_pattern* p, int precision, const void* U,
+                              int64_t ldu, const void* W, int64_t ldw, int32_t k,
+                              const void* a_csr, void* y_csr, double delta, double* sums,
+                              void* stream);
+
+/* ------------------------------------------------------------------ R4SVD */
+/* One call of R4SVD (Algorithm 3; Algorithm 2 when s == 0) on Y given in CSR order
+ * on the pattern.  U_prev: m x s recycled left singular vectors (ld_prev), may be NULL
+ * when s == 0.  The basis grows by Gaussian blocks drawn as svt_gaussian_block(
+ * opt->seed, iter, b, n, w) until the error percentage (||Y||_F^2 - ||B||_F^2) /
+ * ||Y||_F^2 is at most eps_thr or the rank reaches min(m, n, r_max).
+ * Outputs (device, element type of y_csr): U (m x r, ldu) = Q U_B, V (n x r, ldv) the
+ * right singular vectors, S[r] (binary64, host or device) the singular values in
+ * descending order.  Capacities ldu, ldv and S must hold min(m, n, r_max) columns.
+ * *r_out, *eps_out and *blocks_out are host pointers. */
+svt_status svt_r4svd(const svt_pattern* p, const void* y_csr, const void* U_prev,
+                     int64_t ld_prev, int32_t s, double eps_thr, uint32_t iter,
+                     const svt_options* opt, void* U, int64_t ldu, double* S, void* V,
+                     int64_t ldv, int32_t* r_out, double* eps_out, int32_t* blocks_out);
+
+/* ------------------------------------------------------------------ fast SVT */
+/* Algorithm 4: complete the m x n matrix from nnz observed entries (rows, cols, vals).
+ * rows/cols/vals may be host or device pointers (detected per pointer); vals is
+ * double for SVT_FP64 and float for SVT_MIXED_FP32.  tau > 0 is the threshold of
+ * eq. (3), delta > 0 the step of eq. (4); the iteration stops when the relative
+ * residual ||P_Lambda(A - X^(i))||_F / ||P_Lambda(A)||_F falls below tol, or after
+ * maxit iterations (SVT_NOT_CONVERGED).
+ * Output X = U diag(S) V^T with U (m x cap), S[cap], V (n x cap), binary64, row-major,
+ * host or device memory; the first res->k columns are valid.  cap must be at least
+ * min(m, n, r_max).  log (host, may be NULL) receives up to log_cap iteration records.
+ * res (host) is always written. */
+svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                        const int32_t* cols, const void* vals, double tau, double delta,
+                        double tol, int32_t maxit, const svt_options* opt, double* U,
+                        double* S, double* V, int32_t cap, svt_result* res,
+                        svt_iter_log* log, int32_t log_cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVT_GB300_H */

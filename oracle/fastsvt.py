@@ -272,7 +272,7 @@ def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=
         return empty
     As = _sparse(p, a)
     s2 = spectral_norm_estimate(As, seed, power_steps)
-    k0 = int(math.ceil(tau / (delta * s2)))
+    k0 = int(math.ceil(tau / (delta * s2))) if s2 > 0.0 else 1
     y = k0 * delta * a                                       # Y^(0) = k0 delta P_Lambda(A)
     eps_thr = float(eps_thr0)
     eps_min = math.inf

@@ -1,0 +1,267 @@
+"""GB300 (sm_103a) fast singular value thresholding with R4SVD.
+
+Thin Python binding of the C ABI in ``include/svt_gb300.h``: it marshals torch
+tensors (device memory, the current CUDA stream) or numpy arrays (host memory) into
+the library calls; every step of the computation runs in the library's CUDA kernels.
+There is no CPU fallback: without a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "sampled_update",
+           "r4svd", "complete", "library", "FP64", "MIXED_FP32"]
+
+FP64 = L.SVT_FP64
+MIXED_FP32 = L.SVT_MIXED_FP32
+_PREC = {"fp64": FP64, "float64": FP64, "mixed": MIXED_FP32, "fp32": MIXED_FP32,
+         "mixed_fp32": MIXED_FP32, FP64: FP64, MIXED_FP32: MIXED_FP32}
+
+
+class SVTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"svt status {status}: {message}")
+        self.status = status
+
+
+def library():
+    return L.load()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the SVT library needs a CUDA device (no CPU fallback exists)")
+    return torch
+
+
+def _check(st):
+    if st < 0:
+        lib = library()
+        raise SVTError(st, lib.svt_last_error().decode())
+    return st
+
+
+def _prec(p):
+    try:
+        return _PREC[p]
+    except KeyError:
+        raise ValueError(f"unknown precision {p!r}") from None
+
+
+def _vdtype(prec):
+    torch = _torch()
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+def _stream_ptr():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def options(precision="fp64", **kw) -> L.Options:
+    lib = library()
+    o = L.Options()
+    lib.svt_default_options(C.byref(o))
+    o.precision = _prec(precision)
+    for key, val in kw.items():
+        if key == "t" and val is None:
+            continue
+        if not hasattr(o, key):
+            raise TypeError(f"unknown option {key}")
+        setattr(o, key, val)
+    return o
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _cuda_i32(x):
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32))
+    return x.to(device="cuda", dtype=torch.int32).contiguous()
+
+
+class Pattern:
+    """The observed set Lambda sorted into CSR and CSC order on the device."""
+
+    def __init__(self, m, n, rows, cols):
+        torch = _torch()
+        lib = library()
+        self.m, self.n = int(m), int(n)
+        r = _cuda_i32(rows)
+        c = _cuda_i32(cols)
+        h = C.c_void_p()
+        _check(lib.svt_pattern_create(self.m, self.n, r.numel(), _ptr(r), _ptr(c), _stream_ptr(),
+                                      C.byref(h)))
+        self._h = h
+        self.nnz = int(lib.svt_pattern_nnz(h))
+        self._torch = torch
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        torch = self._torch
+        dev = dict(device="cuda", dtype=torch.int32)
+        out = dict(row_ptr=torch.empty(self.m + 1, **dev), col_idx=torch.empty(self.nnz, **dev),
+                   csr_src=torch.empty(self.nnz, **dev), col_ptr=torch.empty(self.n + 1, **dev),
+                   row_idx=torch.empty(self.nnz, **dev), perm=torch.empty(self.nnz, **dev))
+        _check(library().svt_pattern_export(self._h, *[_ptr(out[k]) for k in
+                                            ("row_ptr", "col_idx", "csr_src", "col_ptr", "row_idx",
+                                             "perm")], _stream_ptr()))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            library().svt_pattern_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gaussian_block(seed, it, block, n, w):
+    torch = _torch()
+    out = torch.empty((n, w), device="cuda", dtype=torch.float64)
+    _check(library().svt_gaussian_block(int(seed), int(it) & 0xFFFFFFFF, int(block) & 0xFFFFFFFF, n, w,
+                                        _ptr(out), max(w, 1), _stream_ptr()))
+    return out
+
+
+def spmm(pattern: Pattern, y_csr, W, transpose=False, precision="fp64"):
+    """Y W (transpose False, W n x w) or Y^T W (transpose True, W m x w)."""
+    torch = _torch()
+    prec = _prec(precision)
+    dt = _vdtype(prec)
+    y = y_csr.to(device="cuda", dtype=dt).contiguous()
+    W = W.to(device="cuda", dtype=dt).contiguous()
+    w = W.shape[1]
+    rows = pattern.n if transpose else pattern.m
+    out = torch.empty((rows, w), device="cuda", dtype=dt)
+    _check(library().svt_spmm(pattern.handle, prec, 1 if transpose else 0, _ptr(y), _ptr(W), max(w, 1),
+                              w, _ptr(out), max(w, 1), _stream_ptr()))
+    return out
+
+
+def sampled_update(pattern: Pattern, U, W, a_csr, y_csr, delta, precision="fp64"):
+    """In place on y_csr: y += delta (a - (U W^T) on Lambda); returns (sum d^2, sum |d|, sum y^2)."""
+    prec = _prec(precision)
+    dt = _vdtype(prec)
+    U = U.to(device="cuda", dtype=dt).contiguous()
+    W = W.to(device="cuda", dtype=dt).contiguous()
+    a = a_csr.to(device="cuda", dtype=dt).contiguous()
+    assert y_csr.is_cuda and y_csr.dtype == dt and y_csr.is_contiguous()
+    k = U.shape[1]
+    sums = (C.c_double * 3)()
+    _check(library().svt_sampled_update(pattern.handle, prec, _ptr(U), max(k, 1), _ptr(W), max(k, 1), k,
+                                        _ptr(a), _ptr(y_csr), float(delta), sums, _stream_ptr()))
+    return tuple(sums)
+
+
+def r4svd(pattern: Pattern, y_csr, eps_thr, it, U_prev=None, precision="fp64", **kw):
+    """One R4SVD call (Algorithm 3; Algorithm 2 when U_prev is None)."""
+    torch = _torch()
+    o = options(precision, **kw)
+    o.stream = _stream_ptr().value
+    dt = _vdtype(o.precision)
+    m, n = pattern.m, pattern.n
+    r_cap = min(m, n, o.r_max) if o.r_max > 0 else min(m, n)
+    y = y_csr.to(device="cuda", dtype=dt).contiguous()
+    s = 0 if U_prev is None else int(U_prev.shape[1])
+    Up = None if U_prev is None else U_prev.to(device="cuda", dtype=dt).contiguous()
+    U = torch.zeros((m, r_cap), device="cuda", dtype=dt)
+    V = torch.zeros((n, r_cap), device="cuda", dtype=dt)
+    S = torch.zeros(r_cap, device="cuda", dtype=torch.float64)
+    r, eps, blocks = C.c_int32(0), C.c_double(0), C.c_int32(0)
+    _check(library().svt_r4svd(pattern.handle, _ptr(y), _ptr(Up), max(s, 1), s, float(eps_thr),
+                               int(it) & 0xFFFFFFFF, C.byref(o), _ptr(U), r_cap, _ptr(S), _ptr(V), r_cap,
+                               C.byref(r), C.byref(eps), C.byref(blocks)))
+    rr = r.value
+    return dict(U=U[:, :rr], S=S[:rr], V=V[:, :rr], r=rr, eps=eps.value, blocks=blocks.value)
+
+
+@dataclass
+class Completion:
+    U: object
+    S: object
+    V: object
+    k: int
+    iters: int
+    status: int
+    rel_residual: float
+    mae: float
+    k0: int
+    spec_norm: float
+    r: int
+    seconds_pattern: float
+    seconds_total: float
+    log: list
+
+    @property
+    def converged(self):
+        return self.status == L.SVT_OK
+
+
+def _log_list(buf, n):
+    keys = [f[0] for f in L.IterLog._fields_]
+    return [{k: getattr(buf[i], k) for k in keys} for i in range(n)]
+
+
+def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", log=True,
+             on_host=None, **kw) -> Completion:
+    """Algorithm 4 on (rows, cols, vals).
+
+    Host inputs (numpy) are copied to the device inside the call and the factors come
+    back as numpy arrays; device inputs (torch CUDA tensors) give device outputs.
+    """
+    torch = _torch()
+    o = options(precision, **kw)
+    o.stream = _stream_ptr().value
+    dt = _vdtype(o.precision)
+    r_cap = min(m, n, o.r_max) if o.r_max > 0 else min(m, n)
+    host = isinstance(vals, np.ndarray) if on_host is None else on_host
+    if host:
+        np_dt = np.float64 if o.precision == FP64 else np.float32
+        rows_h = np.ascontiguousarray(rows, dtype=np.int32)
+        cols_h = np.ascontiguousarray(cols, dtype=np.int32)
+        vals_h = np.ascontiguousarray(vals, dtype=np_dt)
+        U = np.zeros((m, r_cap)); S = np.zeros(r_cap); V = np.zeros((n, r_cap))
+        args = [rows_h.ctypes.data_as(C.c_void_p), cols_h.ctypes.data_as(C.c_void_p),
+                vals_h.ctypes.data_as(C.c_void_p)]
+        outs = [U.ctypes.data_as(C.c_void_p), S.ctypes.data_as(C.c_void_p), V.ctypes.data_as(C.c_void_p)]
+        nnz = rows_h.shape[0]
+        keep = (rows_h, cols_h, vals_h)
+    else:
+        rows_d, cols_d = _cuda_i32(rows), _cuda_i32(cols)
+        vals_d = vals.to(device="cuda", dtype=dt).contiguous()
+        U = torch.zeros((m, r_cap), device="cuda", dtype=torch.float64)
+        S = torch.zeros(r_cap, device="cuda", dtype=torch.float64)
+        V = torch.zeros((n, r_cap), device="cuda", dtype=torch.float64)
+        args = [_ptr(rows_d), _ptr(cols_d), _ptr(vals_d)]
+        outs = [_ptr(U), _ptr(S), _ptr(V)]
+        nnz = rows_d.numel()
+        keep = (rows_d, cols_d, vals_d)
+    res = L.Result()
+    log_cap = maxit if log else 0
+    logbuf = (L.IterLog * max(log_cap, 1))()
+    st = library().svt_complete(m, n, nnz, *args, float(tau), float(delta), float(tol), int(maxit),
+                                C.byref(o), *outs, r_cap, C.byref(res), logbuf, log_cap)
+    del keep
+    _check(st)
+    k = res.k
+    return Completion(U=U[:, :k], S=S[:k], V=V[:, :k], k=k, iters=res.iters, status=res.status,
+                      rel_residual=res.rel_residual, mae=res.mae, k0=res.k0, spec_norm=res.spec_norm,
+                      r=res.r, seconds_pattern=res.seconds_pattern, seconds_total=res.seconds_total,
+                      log=_log_list(logbuf, res.log_len))

@@ -1,0 +1,121 @@
+// Shared device helpers, error plumbing and the scratch arena of the SVT library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+
+#include "svt_gb300.h"
+
+namespace svt {
+
+// ---------------------------------------------------------------- error plumbing
+void set_error(const char* fmt, ...);
+svt_status fail(svt_status code, const char* fmt, ...);
+svt_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define SVT_CUDA(expr)                                                        \
+  do {                                                                        \
+    cudaError_t svt_e_ = (expr);                                              \
+    if (svt_e_ != cudaSuccess) return ::svt::cuda_fail(svt_e_, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define SVT_LAUNCH_CHECK() SVT_CUDA(cudaGetLastError())
+
+#define SVT_TRY(expr)                                                         \
+  do {                                                                        \
+    svt_status svt_s_ = (expr);                                               \
+    if (svt_s_ < 0) return svt_s_;                                            \
+  } while (0)
+
+int num_sms();
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).
+// Deterministic: fixed shuffle tree, then warp partials summed in warp order.
+__device__ __forceinline__ double block_sum(double v, double* smem32) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem32[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? smem32[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;  // valid in thread 0 (and the whole of warp 0)
+}
+
+// ---------------------------------------------------------------- device flags
+// Bits raised by kernels into a device status word and read back by the host.
+enum : unsigned {
+  FLAG_INDEX = 1u,       // index out of range in the pattern input
+  FLAG_DUPLICATE = 2u,   // duplicate (row, col)
+  FLAG_NONFINITE = 4u,   // non-finite value met in a reduction
+  FLAG_CHOLESKY = 8u,    // non-positive pivot in a small Cholesky factorisation
+};
+
+// ---------------------------------------------------------------- scratch arena
+// Sub-allocates 256-byte aligned slices from one stream-ordered device block.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = round_up((int64_t)(count * sizeof(T)), 256);
+    if (bytes == 0) bytes = 256;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+// RAII owner of a stream-ordered allocation.
+struct DeviceBlock {
+  void* ptr = nullptr;
+  cudaStream_t stream = nullptr;
+  ~DeviceBlock() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+  }
+  svt_status alloc(size_t bytes, cudaStream_t s);
+};
+
+// Memory location of a user pointer (host or device).
+bool is_device_pointer(const void* p);
+
+}  // namespace svt
+
+// The pattern object behind the opaque ABI handle.
+struct svt_pattern {
+  int64_t m = 0, n = 0, nnz = 0;
+  int32_t* row_ptr = nullptr;   // m+1
+  int32_t* col_idx = nullptr;   // nnz, CSR
+  int32_t* csr_src = nullptr;   // nnz, input position of each CSR slot
+  int32_t* col_ptr = nullptr;   // n+1
+  int32_t* row_idx = nullptr;   // nnz, CSC
+  int32_t* perm = nullptr;      // nnz, CSR slot of each CSC slot
+  int32_t* csr_row = nullptr;   // nnz, row of each CSR slot
+  void* block = nullptr;        // single device allocation holding the arrays
+};

@@ -1,0 +1,84 @@
+// Host-side launchers of the SVT kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace svt {
+
+// pattern.cu ------------------------------------------------------------------
+svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                         const int32_t* cols, cudaStream_t s, svt_pattern** out);
+
+// rng.cu ----------------------------------------------------------------------
+template <typename T>
+svt_status launch_gaussian(uint64_t seed, uint32_t iter, uint32_t blk, int64_t n, int w, T* out,
+                           int64_t ld, cudaStream_t s);
+
+// spmm.cu ---------------------------------------------------------------------
+// out[r, 0:w] = sum_{e in ptr[r]..ptr[r+1]} val[e] * W[idx[e], 0:w] for r < nrows.
+template <typename TV, typename TD>
+svt_status launch_spmm_rows(int64_t nrows, const int32_t* ptr, const int32_t* idx,
+                            const TV* val, const TD* W, int64_t ldw, int w, TD* out,
+                            int64_t ldo, cudaStream_t s);
+// dst[q] = src[perm[q]]
+template <typename T>
+svt_status launch_gather(int64_t count, const int32_t* perm, const T* src, T* dst,
+                         cudaStream_t s);
+
+// dense.cu --------------------------------------------------------------------
+// C (p x q, binary64, ldc) = A^T B with A (M x p), B (M x q), reduction over M split
+// across blocks; `part` must hold gemm_tn_scratch(M, p, q) doubles.
+size_t gemm_tn_scratch(int64_t M, int p, int q);
+template <typename TA, typename TB>
+svt_status gemm_tn(int64_t M, int p, int q, const TA* A, int64_t lda, const TB* B, int64_t ldb,
+                   double* C, int64_t ldc, double* part, cudaStream_t s);
+// C (M x q) = alpha A (M x p) B (p x q) + beta Cin; B binary64; C must not alias A.
+template <typename TA, typename TC>
+svt_status gemm_nn(int64_t M, int p, int q, double alpha, const TA* A, int64_t lda,
+                   const double* B, int64_t ldb, double beta, const TC* Cin, int64_t ldcin,
+                   TC* C, int64_t ldc, cudaStream_t s);
+// sums[c] = sum_i X[i, c]^2 for c < w (binary64), `part` holds colsumsq_scratch doubles.
+size_t colsumsq_scratch(int64_t M, int w);
+template <typename T>
+svt_status colsumsq(int64_t M, int w, const T* X, int64_t ldx, double* sums, double* part,
+                    cudaStream_t s);
+// dst (M x w, ldd) = (TD) src (M x w, lds)
+template <typename TS, typename TD>
+svt_status copy_convert(int64_t M, int w, const TS* src, int64_t lds, TD* dst, int64_t ldd,
+                        cudaStream_t s);
+// Upper Cholesky factor R of the w x w SPD matrix G (R^T R = G) and its inverse, one
+// block; raises FLAG_CHOLESKY and writes min_j R_jj (0 on failure) to *diag_min.
+svt_status chol_inv(int w, const double* G, int64_t ldg, double* R, double* Rinv,
+                    double* work, double* diag_min, unsigned* flags, cudaStream_t s);
+
+// eig.cu ----------------------------------------------------------------------
+size_t eig_scratch(int r);
+// Symmetric eigen-decomposition of the r x r binary64 matrix G (ldg): eigenvalues in
+// descending order (lam), eigenvectors as columns of Ub (r x r, ldu).  FP32 Jacobi
+// start, then binary64 refinement steps built from GEMMs.
+svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
+                   double* work, int refine_steps, cudaStream_t s);
+
+// update.cu -------------------------------------------------------------------
+size_t reduce_scratch();
+// sum of squares of x[0..count) (binary64 result into *out, device)
+template <typename T>
+svt_status sumsq(int64_t count, const T* x, double* out, double* part, cudaStream_t s);
+// y = (T)(scale * a)
+template <typename T>
+svt_status scale_copy(int64_t count, const T* a, double scale, T* y, cudaStream_t s);
+// a_csr[k] = (T) vals[src[k]]
+template <typename TS, typename T>
+svt_status gather_convert(int64_t count, const int32_t* src, const TS* vals, T* a_csr,
+                          cudaStream_t s);
+// Sampled shrinkage + update over CSR rows; out3 (device) = {sum d^2, sum |d|, sum y^2}.
+template <typename T>
+svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W,
+                          int64_t ldw, int k, const T* a, T* y, double delta, double* out3,
+                          double* part, unsigned* flags, cudaStream_t s);
+
+}  // namespace svt

@@ -1,0 +1,751 @@
+// Fast SVT driver (Algorithm 4) and R4SVD (Algorithm 3; Algorithm 2 on iteration 1).
+//
+// Host code here only sequences kernels and takes the scalar decisions of the
+// algorithms (rank growth, cooling, stopping) from binary64 values read back after
+// each step; every vector and matrix operation runs in the library's kernels.
+//
+// Readings of points the paper leaves open (shared with the CPU reference):
+//  - residual eps^(i) = ||P_Lambda(A - X^(i))||_F / ||P_Lambda(A)||_F, after D_tau;
+//    per iteration: R4SVD -> residual -> cooling -> stop (strict <) -> update;
+//  - Y^(0) = k0 delta P_Lambda(A), k0 = ceil(tau / (delta ||P_Lambda(A)||_2)), the norm
+//    from a fixed number of power steps from a seeded Gaussian start vector;
+//  - power iterations X <- Y (Y^T X); QB error (||Y||^2 - ||B||^2) / ||Y||^2;
+//  - new blocks are appended, orthogonalised against Q twice, and the range counts
+//    as exhausted (block discarded, loop ended) when the smallest diagonal entry of
+//    the block's triangular factor is at most 1e-7 of its largest column norm;
+//  - the first iteration draws a block of width min(t, r_cap) unconditionally; all r
+//    columns of U are recycled; r_cap = min(m, n, r_max);
+//  - D_tau keeps sigma_j > tau.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace svt {
+
+// ------------------------------------------------------------------ error plumbing
+static thread_local char g_err[512] = "no error";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+svt_status fail(svt_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+svt_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  set_error("CUDA error '%s' in %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+  return SVT_ERR_CUDA;
+}
+
+int num_sms() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      cached = v;
+    else
+      return 132;
+  }
+  return cached;
+}
+
+bool is_device_pointer(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+svt_status DeviceBlock::alloc(size_t bytes, cudaStream_t s) {
+  static std::once_flag once;
+  std::call_once(once, []() {
+    // keep freed stream-ordered memory in the pool between calls
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+  stream = s;
+  SVT_CUDA(cudaMallocAsync(&ptr, bytes > 0 ? bytes : 256, s));
+  return SVT_OK;
+}
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+double seconds_since(clk::time_point t0) {
+  return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+constexpr double kExhaustedRel = 1e-7;
+constexpr uint32_t kPowerSeedIter = 0xFFFFFFFFu;
+constexpr int kRefineSteps = 3;
+
+struct Params {
+  int64_t m, n;
+  int r_cap, t_eff, dt, np, power_steps;
+  double beta, eps_thr0;
+  uint64_t seed;
+};
+
+svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params* P) {
+  if (!o) return fail(SVT_ERR_ARG, "null options");
+  if (o->dt <= 0 || o->n_power < 0 || !(o->beta > 0.0 && o->beta < 1.0) || o->power_steps < 1)
+    return fail(SVT_ERR_ARG, "options: need dt > 0, n_power >= 0, 0 < beta < 1, power_steps >= 1");
+  if (o->precision != SVT_FP64 && o->precision != SVT_MIXED_FP32)
+    return fail(SVT_ERR_ARG, "options: unknown precision %d", o->precision);
+  const int64_t mn = std::min(m, n);
+  int64_t cap = o->r_max > 0 ? std::min<int64_t>(mn, o->r_max) : mn;
+  if (cap > 1024)
+    return fail(SVT_ERR_UNSUPPORTED, "rank cap min(m, n, r_max) = %lld exceeds 1024; set r_max",
+                (long long)cap);
+  int64_t t = o->t > 0 ? o->t : (int64_t)std::floor(0.05 * (double)mn);
+  if (t < 1) t = 1;
+  P->m = m; P->n = n; P->r_cap = (int)cap; P->t_eff = (int)std::min<int64_t>(t, 1 << 20);
+  P->dt = o->dt; P->np = o->n_power; P->power_steps = o->power_steps;
+  P->beta = o->beta; P->eps_thr0 = o->eps_thr0; P->seed = o->seed;
+  return SVT_OK;
+}
+
+inline int64_t ld_of(int64_t cols) { return round_up(cols > 0 ? cols : 1, 4); }
+
+template <typename T>
+__global__ void k_scale_cols(int r, int k, const double* __restrict__ Ub, int64_t ldu,
+                             const double* __restrict__ coef, double* __restrict__ out) {
+  const int64_t total = (int64_t)r * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / k), j = (int)(t % k);
+    out[t] = Ub[(int64_t)i * ldu + j] * coef[j];
+  }
+}
+
+__global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ ss,
+                            double* __restrict__ v) {
+  const double inv = 1.0 / sqrt(ss[0]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * inv;
+}
+
+// Device buffers of one solve (or one R4SVD call).
+template <typename T>
+struct Work {
+  Params P;
+  const svt_pattern* pat = nullptr;
+  cudaStream_t s = nullptr;
+  int wmax = 1;
+  int64_t ldq = 0, ldb = 0, ldw = 0, ldk = 0;
+  T *Qa = nullptr, *Qb = nullptr;   // m x ldq (basis / recycled U, ping-pong)
+  T *Bt = nullptr;                  // n x ldb
+  T *Om = nullptr, *Z = nullptr;    // n x ldw
+  T *X = nullptr, *X2 = nullptr;    // m x ldw
+  T *Wk = nullptr;                  // n x ldk (V_K scaled by sigma - tau, or V)
+  T *y_csc = nullptr;               // nnz
+  double *G = nullptr, *Ub = nullptr, *lam = nullptr, *Gs = nullptr;
+  double *Gx = nullptr, *Rm = nullptr, *Rinv = nullptr, *cwork = nullptr, *Tsm = nullptr;
+  double *coef = nullptr, *part = nullptr, *eigw = nullptr, *dsc = nullptr, *colss = nullptr;
+  double *pv = nullptr, *pu = nullptr, *pw = nullptr;  // power-iteration vectors
+  unsigned* flags = nullptr;
+
+  void layout(Arena& a) {
+    const int64_t m = P.m, n = P.n, z = pat->nnz;
+    const int rc = P.r_cap;
+    wmax = std::max(std::min(P.t_eff, rc), std::min(P.dt, rc));
+    ldq = ld_of(rc); ldb = ld_of(rc); ldw = ld_of(wmax); ldk = ld_of(rc);
+    Qa = a.take<T>(m * ldq); Qb = a.take<T>(m * ldq);
+    Bt = a.take<T>(n * ldb);
+    Om = a.take<T>(n * ldw); Z = a.take<T>(n * ldw);
+    X = a.take<T>(m * ldw); X2 = a.take<T>(m * ldw);
+    Wk = a.take<T>(n * ldk);
+    y_csc = a.take<T>(z);
+    G = a.take<double>((int64_t)rc * rc);
+    Ub = a.take<double>((int64_t)rc * rc);
+    lam = a.take<double>(rc);
+    Gs = a.take<double>((int64_t)rc * wmax);
+    Gx = a.take<double>((int64_t)wmax * wmax);
+    Rm = a.take<double>((int64_t)wmax * wmax);
+    Rinv = a.take<double>((int64_t)wmax * wmax);
+    cwork = a.take<double>((int64_t)wmax * wmax);
+    Tsm = a.take<double>((int64_t)rc * rc);
+    coef = a.take<double>(rc);
+    size_t pe = reduce_scratch();
+    pe = std::max(pe, gemm_tn_scratch(m, rc, wmax));
+    pe = std::max(pe, gemm_tn_scratch(m, wmax, wmax));
+    pe = std::max(pe, gemm_tn_scratch(n, rc, rc));
+    pe = std::max(pe, colsumsq_scratch(std::max(m, n), std::max(wmax, rc)));
+    part = a.take<double>(pe);
+    eigw = a.take<double>(eig_scratch(rc));
+    dsc = a.take<double>(16);
+    colss = a.take<double>(std::max(wmax, rc));
+    pv = a.take<double>(n); pw = a.take<double>(n); pu = a.take<double>(m);
+    flags = a.take<unsigned>(4);
+  }
+};
+
+template <typename T>
+svt_status read_flags(Work<T>& W, unsigned* out) {
+  SVT_CUDA(cudaMemcpyAsync(out, W.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  return SVT_OK;
+}
+
+// Sum of squares of columns [c0, c0+w) of an M x w block, summed on the host in column order.
+template <typename T>
+svt_status block_sumsq(Work<T>& W, int64_t M, int w, const T* X, int64_t ldx, double* out,
+                       double* maxcol = nullptr) {
+  std::vector<double> h(w > 0 ? w : 1);
+  if (w <= 0) { *out = 0.0; if (maxcol) *maxcol = 0.0; return SVT_OK; }
+  SVT_TRY(colsumsq<T>(M, w, X, ldx, W.colss, W.part, W.s));
+  SVT_CUDA(cudaMemcpyAsync(h.data(), W.colss, w * sizeof(double), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  double s = 0.0, mx = 0.0;
+  for (int c = 0; c < w; ++c) { s += h[c]; mx = std::max(mx, h[c]); }
+  *out = s;
+  if (maxcol) *maxcol = std::sqrt(mx);
+  return SVT_OK;
+}
+
+struct R4Out {
+  int r = 0, blocks = 0;
+  bool exhausted = false;
+  double eps = 0.0, normB = 0.0;
+  std::vector<double> sigma;  // descending, r entries
+};
+
+// Algorithm 3 (Algorithm 2 when s == 0).  Q holds the recycled basis in columns [0, s);
+// new blocks are appended in place.  On return U = Q U_B is written to Unew (m x ldq),
+// Bt (n x r) = Y^T Q, W.Ub = U_B, sigma on the host.
+template <typename T>
+svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, double normY2,
+                     double eps_thr, uint32_t iter, T* Unew, R4Out* o) {
+  const Params& P = W.P;
+  const svt_pattern* p = W.pat;
+  const int64_t m = P.m, n = P.n;
+  cudaStream_t st = W.s;
+  int r = s;
+  double normB = 0.0;
+  if (s > 0) {
+    SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, st)));
+    SVT_TRY(block_sumsq<T>(W, n, s, W.Bt, W.ldb, &normB));
+  }
+  auto eps_of = [&](double nb) { return normY2 > 0.0 ? (normY2 - nb) / normY2 : 0.0; };
+  double eps = eps_of(normB);
+  bool first = (s == 0);
+  int blocks = 0;
+  bool exhausted = false;
+  while ((first || eps > eps_thr) && r < P.r_cap) {
+    const int w = first ? std::min(P.t_eff, P.r_cap) : std::min(P.dt, P.r_cap - r);
+    SVT_TRY(launch_gaussian<T>(P.seed, iter, (uint32_t)blocks, n, w, W.Om, W.ldw, st));
+    ++blocks;
+    SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, st)));
+    for (int it = 0; it < P.np; ++it) {
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, W.X, W.ldw, w, W.Z, W.ldw, st)));
+      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Z, W.ldw, w, W.X, W.ldw, st)));
+    }
+    double ssum = 0.0, scale = 0.0;
+    SVT_TRY(block_sumsq<T>(W, m, w, W.X, W.ldw, &ssum, &scale));
+    if (r > 0) {
+      for (int pass = 0; pass < 2; ++pass) {  // X <- X - Q (Q^T X), twice
+        SVT_TRY((gemm_tn<T, T>(m, r, w, Q, W.ldq, W.X, W.ldw, W.Gs, w, W.part, st)));
+        SVT_TRY((gemm_nn<T, T>(m, r, w, -1.0, Q, W.ldq, W.Gs, w, 1.0, W.X, W.ldw, W.X2, W.ldw, st)));
+        std::swap(W.X, W.X2);
+      }
+    }
+    // Cholesky-QR, twice: X = Q' R
+    SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
+    SVT_TRY((gemm_tn<T, T>(m, w, w, W.X, W.ldw, W.X, W.ldw, W.Gx, w, W.part, st)));
+    SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 0, W.flags, st));
+    double dmin = 0.0;
+    unsigned fl = 0;
+    SVT_CUDA(cudaMemcpyAsync(&dmin, W.dsc + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SVT_TRY(read_flags(W, &fl));
+    if (scale == 0.0 || (fl & FLAG_CHOLESKY) || !(dmin > kExhaustedRel * scale)) {
+      exhausted = true;
+      break;
+    }
+    SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X, W.ldw, W.Rinv, w, 0.0, nullptr, 0, W.X2, W.ldw, st)));
+    SVT_TRY((gemm_tn<T, T>(m, w, w, W.X2, W.ldw, W.X2, W.ldw, W.Gx, w, W.part, st)));
+    SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 1, W.flags, st));
+    SVT_TRY(read_flags(W, &fl));
+    if (fl & FLAG_CHOLESKY) return fail(SVT_ERR_NUMERIC, "R4SVD: Cholesky-QR breakdown in block %d", blocks);
+    SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X2, W.ldw, W.Rinv, w, 0.0, nullptr, 0, Q + r, W.ldq, st)));
+    // B'^T = Y^T Q'
+    SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q + r, W.ldq, w, W.Bt + r, W.ldb, st)));
+    double nb = 0.0;
+    SVT_TRY(block_sumsq<T>(W, n, w, W.Bt + r, W.ldb, &nb));
+    normB += nb;
+    r += w;
+    eps = eps_of(normB);
+    first = false;
+  }
+  o->r = r; o->blocks = blocks; o->exhausted = exhausted; o->eps = eps; o->normB = normB;
+  o->sigma.assign(r, 0.0);
+  if (r == 0) return SVT_OK;
+  // svt(B): eigen-decomposition of B B^T = (B^T)^T B^T
+  SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
+  SVT_TRY(sym_eig(r, W.G, r, W.lam, W.Ub, r, W.eigw, kRefineSteps, st));
+  std::vector<double> lam(r);
+  SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // U = Q U_B (all r columns are recycled)
+  SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+  SVT_CUDA(cudaStreamSynchronize(st));
+  for (int j = 0; j < r; ++j) {
+    if (!std::isfinite(lam[j])) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
+    o->sigma[j] = std::sqrt(std::max(lam[j], 0.0));
+  }
+  return SVT_OK;
+}
+
+// Wk (n x k) = Bt (n x r) * Ub[:, :k] diag(coef)
+template <typename T>
+svt_status scaled_right(Work<T>& W, int r, int k, const std::vector<double>& coef) {
+  if (k <= 0) return SVT_OK;
+  SVT_CUDA(cudaMemcpyAsync(W.coef, coef.data(), k * sizeof(double), cudaMemcpyHostToDevice, W.s));
+  const int64_t total = (int64_t)r * k;
+  k_scale_cols<T><<<(int)std::min<int64_t>(ceil_div(total, 256), 1024), 256, 0, W.s>>>(
+      r, k, W.Ub, r, W.coef, W.Tsm);
+  SVT_LAUNCH_CHECK();
+  SVT_TRY((gemm_nn<T, T>(W.P.n, r, k, 1.0, W.Bt, W.ldb, W.Tsm, k, 0.0, nullptr, 0, W.Wk, W.ldk, W.s)));
+  return SVT_OK;
+}
+
+// Copy the first k columns of a device T matrix into caller memory (double, ld = cap).
+template <typename T>
+svt_status export_cols(Work<T>& W, int64_t rows, int k, const T* src, int64_t lds, double* dst,
+                       int cap) {
+  if (rows <= 0 || cap <= 0) return SVT_OK;
+  const bool dev = is_device_pointer(dst);
+  if (dev) {
+    SVT_CUDA(cudaMemsetAsync(dst, 0, rows * cap * sizeof(double), W.s));
+    SVT_TRY((copy_convert<T, double>(rows, k, src, lds, dst, cap, W.s)));
+    return SVT_OK;
+  }
+  DeviceBlock tmp;
+  SVT_TRY(tmp.alloc(rows * cap * sizeof(double), W.s));
+  double* d = (double*)tmp.ptr;
+  SVT_CUDA(cudaMemsetAsync(d, 0, rows * cap * sizeof(double), W.s));
+  SVT_TRY((copy_convert<T, double>(rows, k, src, lds, d, cap, W.s)));
+  SVT_CUDA(cudaMemcpyAsync(dst, d, rows * cap * sizeof(double), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  return SVT_OK;
+}
+
+template <typename T>
+svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                         const int32_t* cols, const T* vals, double tau, double delta,
+                         double tol, int32_t maxit, const svt_options* opt, double* Uo,
+                         double* So, double* Vo, int32_t cap, svt_result* res,
+                         svt_iter_log* log, int32_t log_cap) {
+  const auto t_start = clk::now();
+  Params P;
+  SVT_TRY(make_params(m, n, opt, &P));
+  if (cap < P.r_cap) return fail(SVT_ERR_ARG, "output capacity %d below the rank cap %d", cap, P.r_cap);
+  cudaStream_t st = (cudaStream_t)opt->stream;
+
+  // Inputs to device (copied when the caller passes host memory).
+  DeviceBlock in_blk;
+  const int32_t* d_rows = rows;
+  const int32_t* d_cols = cols;
+  const T* d_vals = vals;
+  if (nnz > 0) {
+    const bool dr = is_device_pointer(rows), dc = is_device_pointer(cols), dv = is_device_pointer(vals);
+    if (!dr || !dc || !dv) {
+      Arena a;
+      a.take<int32_t>(nnz); a.take<int32_t>(nnz); a.take<T>(nnz);
+      SVT_TRY(in_blk.alloc(a.off, st));
+      Arena b; b.base = (char*)in_blk.ptr;
+      int32_t* r2 = b.take<int32_t>(nnz);
+      int32_t* c2 = b.take<int32_t>(nnz);
+      T* v2 = b.take<T>(nnz);
+      if (!dr) { SVT_CUDA(cudaMemcpyAsync(r2, rows, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st)); d_rows = r2; }
+      if (!dc) { SVT_CUDA(cudaMemcpyAsync(c2, cols, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st)); d_cols = c2; }
+      if (!dv) { SVT_CUDA(cudaMemcpyAsync(v2, vals, nnz * sizeof(T), cudaMemcpyHostToDevice, st)); d_vals = v2; }
+    }
+  }
+  svt_pattern* pat = nullptr;
+  const auto t_pat = clk::now();
+  SVT_TRY(build_pattern(m, n, nnz, d_rows, d_cols, st, &pat));
+  struct PatGuard { svt_pattern* p; ~PatGuard() { svt_pattern_destroy(p); } } pg{pat};
+  res->seconds_pattern = seconds_since(t_pat);
+
+  auto zero_outputs = [&]() -> svt_status {
+    // X = 0: k = 0, outputs cleared
+    std::vector<double> zeros;
+    auto clear = [&](double* p, int64_t count) -> svt_status {
+      if (!p || count <= 0) return SVT_OK;
+      if (is_device_pointer(p)) { SVT_CUDA(cudaMemsetAsync(p, 0, count * sizeof(double), st)); }
+      else memset(p, 0, count * sizeof(double));
+      return SVT_OK;
+    };
+    SVT_TRY(clear(Uo, m * cap));
+    SVT_TRY(clear(So, cap));
+    SVT_TRY(clear(Vo, n * cap));
+    SVT_CUDA(cudaStreamSynchronize(st));
+    return SVT_OK;
+  };
+
+  res->k = 0; res->r = 0; res->iters = 0; res->k0 = 0; res->log_len = 0;
+  res->rel_residual = 0.0; res->mae = 0.0; res->spec_norm = 0.0; res->eps_thr = P.eps_thr0;
+  if (nnz == 0) {
+    SVT_TRY(zero_outputs());
+    res->status = SVT_OK;
+    res->seconds_total = seconds_since(t_start);
+    return SVT_OK;
+  }
+
+  Work<T> W;
+  W.P = P; W.pat = pat; W.s = st;
+  Arena a;
+  T* a_csr = a.take<T>(nnz);
+  T* y_csr = a.take<T>(nnz);
+  W.layout(a);
+  DeviceBlock wblk;
+  SVT_TRY(wblk.alloc(a.off, st));
+  Arena b; b.base = (char*)wblk.ptr;
+  a_csr = b.take<T>(nnz);
+  y_csr = b.take<T>(nnz);
+  W.layout(b);
+  SVT_CUDA(cudaMemsetAsync(W.flags, 0, 4 * sizeof(unsigned), st));
+
+  // P_Lambda(A) in CSR order; reject non-finite values.
+  SVT_TRY((gather_convert<T, T>(nnz, pat->csr_src, d_vals, a_csr, st)));
+  double nA2 = 0.0;
+  SVT_TRY(sumsq<T>(nnz, a_csr, W.dsc + 2, W.part, st));
+  SVT_CUDA(cudaMemcpyAsync(&nA2, W.dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SVT_CUDA(cudaStreamSynchronize(st));
+  if (!std::isfinite(nA2)) return fail(SVT_ERR_NUMERIC, "non-finite observed value");
+  if (nA2 == 0.0) {
+    SVT_TRY(zero_outputs());
+    res->status = SVT_OK;
+    res->seconds_total = seconds_since(t_start);
+    return SVT_OK;
+  }
+  const double nA = std::sqrt(nA2);
+
+  // ||P_Lambda(A)||_2 by power steps v <- A^T A v / ||A^T A v|| (a_csc staged in y_csc)
+  SVT_TRY(launch_gather<T>(nnz, pat->perm, a_csr, W.y_csc, st));
+  SVT_TRY(launch_gaussian<double>(P.seed, kPowerSeedIter, 0, n, 1, W.pw, 1, st));
+  SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
+  k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
+  SVT_LAUNCH_CHECK();
+  for (int it = 0; it < P.power_steps; ++it) {
+    SVT_TRY((launch_spmm_rows<T, double>(m, pat->row_ptr, pat->col_idx, a_csr, W.pv, 1, 1, W.pu, 1, st)));
+    SVT_TRY((launch_spmm_rows<T, double>(n, pat->col_ptr, pat->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1, st)));
+    SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
+    k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
+    SVT_LAUNCH_CHECK();
+  }
+  double lam2 = 0.0;
+  SVT_CUDA(cudaMemcpyAsync(&lam2, W.dsc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SVT_CUDA(cudaStreamSynchronize(st));
+  const double s2 = std::sqrt(std::sqrt(lam2));
+  const double kk = s2 > 0.0 ? std::ceil(tau / (delta * s2)) : 1.0;
+  const int k0 = (int)std::min(kk, 2.0e9);
+  res->k0 = k0;
+  res->spec_norm = s2;
+  SVT_TRY(scale_copy<T>(nnz, a_csr, (double)k0 * delta, y_csr, st));
+  SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
+  double normY2 = 0.0;
+  SVT_TRY(sumsq<T>(nnz, y_csr, W.dsc + 4, W.part, st));
+  SVT_CUDA(cudaMemcpyAsync(&normY2, W.dsc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+  SVT_CUDA(cudaStreamSynchronize(st));
+
+  double eps_thr = P.eps_thr0, eps_min = INFINITY;
+  int s = 0;
+  T* Qcur = W.Qa;
+  T* Qnext = W.Qb;
+  int k = 0;
+  R4Out ro;
+  double rel = 0.0, mae = 0.0;
+  int last_iter = 0;
+  svt_status status = SVT_NOT_CONVERGED;
+  std::vector<double> coef;
+  for (int i = 1; i <= maxit; ++i) {
+    const auto t_it = clk::now();
+    SVT_TRY(r4svd_run<T>(W, y_csr, W.y_csc, Qcur, s, normY2, eps_thr, (uint32_t)i, Qnext, &ro));
+    const int r = ro.r;
+    k = 0;
+    while (k < r && ro.sigma[k] > tau) ++k;
+    coef.assign(k, 0.0);
+    for (int j = 0; j < k; ++j) coef[j] = (ro.sigma[j] - tau) / ro.sigma[j];
+    SVT_TRY(scaled_right<T>(W, r, k, coef));
+    SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
+    SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
+                              W.part, W.flags, st));
+    double sums[3];
+    unsigned fl = 0;
+    SVT_CUDA(cudaMemcpyAsync(sums, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SVT_TRY(read_flags(W, &fl));
+    rel = std::sqrt(sums[0]) / nA;
+    mae = sums[1] / (double)nnz;
+    if (!std::isfinite(rel) || (fl & FLAG_NONFINITE))
+      return fail(SVT_ERR_NUMERIC, "non-finite iterate at SVT iteration %d", i);
+    const double thr_used = eps_thr;
+    bool cooled = false;
+    if (rel < eps_min) eps_min = rel;
+    else { eps_thr *= P.beta; cooled = true; }
+    last_iter = i;
+    if (log && i - 1 < log_cap) {
+      svt_iter_log& L = log[i - 1];
+      L.iter = i; L.r = r; L.k = k; L.blocks = ro.blocks; L.cooled = cooled ? 1 : 0;
+      L.exhausted = ro.exhausted ? 1 : 0; L.eps = ro.eps; L.eps_thr = thr_used;
+      L.rel_residual = rel; L.mae = mae; L.sigma_max = r > 0 ? ro.sigma[0] : 0.0;
+      L.seconds = seconds_since(t_it);
+      res->log_len = i;
+    }
+    res->r = r;
+    if (rel < tol) { status = SVT_OK; break; }
+    // Y^(i+1) is already in y_csr (the update ran in the fused pass); refresh its CSC copy
+    SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
+    normY2 = sums[2];
+    std::swap(Qcur, Qnext);
+    s = r;
+  }
+  res->iters = last_iter;
+  res->k = k;
+  res->rel_residual = rel;
+  res->mae = mae;
+  res->eps_thr = eps_thr;
+  res->status = status;
+  if (last_iter == 0) {
+    SVT_TRY(zero_outputs());
+    res->seconds_total = seconds_since(t_start);
+    return status;
+  }
+  // X = U_K diag(sigma_K - tau) V_K^T with V_K = B^T U_B,K Sigma_K^-1
+  std::vector<double> inv(k), shrunk(cap, 0.0);
+  for (int j = 0; j < k; ++j) { inv[j] = 1.0 / ro.sigma[j]; shrunk[j] = ro.sigma[j] - tau; }
+  SVT_TRY(scaled_right<T>(W, ro.r, k, inv));
+  T* Ufinal = (last_iter > 0 && status == SVT_OK) ? Qnext : Qcur;
+  // after a converged break Qnext holds U; after the loop ran out, the swap moved it to Qcur
+  SVT_TRY(export_cols<T>(W, m, k, Ufinal, W.ldq, Uo, cap));
+  SVT_TRY(export_cols<T>(W, n, k, W.Wk, W.ldk, Vo, cap));
+  if (So) SVT_CUDA(cudaMemcpyAsync(So, shrunk.data(), cap * sizeof(double), cudaMemcpyDefault, st));
+  SVT_CUDA(cudaStreamSynchronize(st));
+  res->seconds_total = seconds_since(t_start);
+  return status;
+}
+
+template <typename T>
+svt_status r4svd_impl(const svt_pattern* p, const T* y_csr, const T* U_prev, int64_t ld_prev,
+                      int32_t s, double eps_thr, uint32_t iter, const svt_options* opt, T* U,
+                      int64_t ldu, double* S, T* V, int64_t ldv, int32_t* r_out,
+                      double* eps_out, int32_t* blocks_out) {
+  Params P;
+  SVT_TRY(make_params(p->m, p->n, opt, &P));
+  if (s < 0 || s > P.r_cap) return fail(SVT_ERR_ARG, "r4svd: recycled rank %d outside [0, %d]", s, P.r_cap);
+  if (s > 0 && (!U_prev || ld_prev < s)) return fail(SVT_ERR_ARG, "r4svd: bad recycled basis");
+  if (!U || !V || ldu < P.r_cap || ldv < P.r_cap)
+    return fail(SVT_ERR_ARG, "r4svd: outputs need capacity for %d columns", P.r_cap);
+  cudaStream_t st = (cudaStream_t)opt->stream;
+  Work<T> W;
+  W.P = P; W.pat = p; W.s = st;
+  Arena a;
+  W.layout(a);
+  DeviceBlock blk;
+  SVT_TRY(blk.alloc(a.off, st));
+  Arena b; b.base = (char*)blk.ptr;
+  W.layout(b);
+  SVT_CUDA(cudaMemsetAsync(W.flags, 0, 4 * sizeof(unsigned), st));
+  const int64_t nnz = p->nnz;
+  SVT_TRY(launch_gather<T>(nnz, p->perm, y_csr, W.y_csc, st));
+  double normY2 = 0.0;
+  SVT_TRY(sumsq<T>(nnz, y_csr, W.dsc + 4, W.part, st));
+  SVT_CUDA(cudaMemcpyAsync(&normY2, W.dsc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (s > 0) SVT_TRY((copy_convert<T, T>(p->m, s, U_prev, ld_prev, W.Qa, W.ldq, st)));
+  SVT_CUDA(cudaStreamSynchronize(st));
+  R4Out ro;
+  SVT_TRY(r4svd_run<T>(W, y_csr, W.y_csc, W.Qa, s, normY2, eps_thr, iter, W.Qb, &ro));
+  const int r = ro.r;
+  std::vector<double> inv(r);
+  for (int j = 0; j < r; ++j) inv[j] = ro.sigma[j] > 0.0 ? 1.0 / ro.sigma[j] : 0.0;
+  SVT_TRY(scaled_right<T>(W, r, r, inv));
+  SVT_TRY((copy_convert<T, T>(p->m, r, W.Qb, W.ldq, U, ldu, st)));
+  SVT_TRY((copy_convert<T, T>(p->n, r, W.Wk, W.ldk, V, ldv, st)));
+  if (S && r > 0) SVT_CUDA(cudaMemcpyAsync(S, ro.sigma.data(), r * sizeof(double), cudaMemcpyDefault, st));
+  SVT_CUDA(cudaStreamSynchronize(st));
+  if (r_out) *r_out = r;
+  if (eps_out) *eps_out = ro.eps;
+  if (blocks_out) *blocks_out = ro.blocks;
+  return SVT_OK;
+}
+
+}  // namespace
+}  // namespace svt
+
+// ====================================================================== C ABI
+extern "C" int svt_abi_version(void) { return 1; }
+
+extern "C" void svt_default_options(svt_options* o) {
+  if (!o) return;
+  o->t = -1;
+  o->dt = 10;
+  o->n_power = 0;
+  o->r_max = 0;
+  o->power_steps = 100;
+  o->precision = SVT_FP64;
+  o->beta = 0.95;
+  o->eps_thr0 = 0.9;
+  o->seed = 0x5EEDull;
+  o->stream = nullptr;
+}
+
+extern "C" const char* svt_status_string(int s) {
+  switch (s) {
+    case SVT_OK: return "ok";
+    case SVT_NOT_CONVERGED: return "not converged within maxit";
+    case SVT_ERR_ARG: return "invalid argument";
+    case SVT_ERR_INDEX: return "observed index out of range";
+    case SVT_ERR_DUPLICATE: return "duplicate observed entry";
+    case SVT_ERR_CUDA: return "CUDA runtime error";
+    case SVT_ERR_NUMERIC: return "non-finite value";
+    case SVT_ERR_UNSUPPORTED: return "unsupported size";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* svt_last_error(void) { return svt::g_err; }
+
+extern "C" svt_status svt_spmm(const svt_pattern* p, int precision, int transpose, const void* y_csr,
+                               const void* W, int64_t ldw, int32_t w, void* out, int64_t ldo,
+                               void* stream) {
+  using namespace svt;
+  if (!p || w < 0 || (p->nnz > 0 && !y_csr)) return fail(SVT_ERR_ARG, "spmm: bad arguments");
+  const int64_t rows_out = transpose ? p->n : p->m;
+  const int64_t rows_in = transpose ? p->m : p->n;
+  if (w > 0 && (!W || !out || ldw < w || ldo < w)) return fail(SVT_ERR_ARG, "spmm: bad dense operands");
+  (void)rows_in;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t z = p->nnz;
+  if (w == 0) return SVT_OK;
+  if (precision == SVT_FP64) {
+    const double* y = (const double*)y_csr;
+    DeviceBlock tmp;
+    if (transpose) {
+      SVT_TRY(tmp.alloc(z * sizeof(double), s));
+      SVT_TRY(launch_gather<double>(z, p->perm, y, (double*)tmp.ptr, s));
+      SVT_TRY((launch_spmm_rows<double, double>(rows_out, p->col_ptr, p->row_idx, (double*)tmp.ptr,
+                                                 (const double*)W, ldw, w, (double*)out, ldo, s)));
+    } else {
+      SVT_TRY((launch_spmm_rows<double, double>(rows_out, p->row_ptr, p->col_idx, y,
+                                                 (const double*)W, ldw, w, (double*)out, ldo, s)));
+    }
+    SVT_CUDA(cudaStreamSynchronize(s));
+  } else if (precision == SVT_MIXED_FP32) {
+    const float* y = (const float*)y_csr;
+    DeviceBlock tmp;
+    if (transpose) {
+      SVT_TRY(tmp.alloc(z * sizeof(float), s));
+      SVT_TRY(launch_gather<float>(z, p->perm, y, (float*)tmp.ptr, s));
+      SVT_TRY((launch_spmm_rows<float, float>(rows_out, p->col_ptr, p->row_idx, (float*)tmp.ptr,
+                                               (const float*)W, ldw, w, (float*)out, ldo, s)));
+    } else {
+      SVT_TRY((launch_spmm_rows<float, float>(rows_out, p->row_ptr, p->col_idx, y, (const float*)W,
+                                               ldw, w, (float*)out, ldo, s)));
+    }
+    SVT_CUDA(cudaStreamSynchronize(s));
+  } else {
+    return fail(SVT_ERR_ARG, "spmm: unknown precision");
+  }
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_sampled_update(const svt_pattern* p, int precision, const void* U,
+                                         int64_t ldu, const void* W, int64_t ldw, int32_t k,
+                                         const void* a_csr, void* y_csr, double delta, double* sums,
+                                         void* stream) {
+  using namespace svt;
+  if (!p || k < 0 || !sums || (k > 0 && (!U || !W || ldu < k || ldw < k)))
+    return fail(SVT_ERR_ARG, "sampled_update: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceBlock blk;
+  const size_t pe = reduce_scratch();
+  SVT_TRY(blk.alloc(pe * sizeof(double) + 64 + 256, s));
+  double* part = (double*)blk.ptr;
+  double* out3 = part + pe;
+  unsigned* flags = (unsigned*)(out3 + 4);
+  SVT_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
+  if (precision == SVT_FP64)
+    SVT_TRY(sampled_update<double>(p, (const double*)U, ldu, (const double*)W, ldw, k,
+                                   (const double*)a_csr, (double*)y_csr, delta, out3, part, flags, s));
+  else if (precision == SVT_MIXED_FP32)
+    SVT_TRY(sampled_update<float>(p, (const float*)U, ldu, (const float*)W, ldw, k,
+                                  (const float*)a_csr, (float*)y_csr, delta, out3, part, flags, s));
+  else
+    return fail(SVT_ERR_ARG, "sampled_update: unknown precision");
+  SVT_CUDA(cudaMemcpyAsync(sums, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SVT_CUDA(cudaStreamSynchronize(s));
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_r4svd(const svt_pattern* p, const void* y_csr, const void* U_prev,
+                                int64_t ld_prev, int32_t s, double eps_thr, uint32_t iter,
+                                const svt_options* opt, void* U, int64_t ldu, double* S, void* V,
+                                int64_t ldv, int32_t* r_out, double* eps_out, int32_t* blocks_out) {
+  using namespace svt;
+  if (!p || !opt || (p->nnz > 0 && !y_csr)) return fail(SVT_ERR_ARG, "r4svd: bad arguments");
+  if (opt->precision == SVT_FP64)
+    return r4svd_impl<double>(p, (const double*)y_csr, (const double*)U_prev, ld_prev, s, eps_thr,
+                              iter, opt, (double*)U, ldu, S, (double*)V, ldv, r_out, eps_out,
+                              blocks_out);
+  if (opt->precision == SVT_MIXED_FP32)
+    return r4svd_impl<float>(p, (const float*)y_csr, (const float*)U_prev, ld_prev, s, eps_thr, iter,
+                             opt, (float*)U, ldu, S, (float*)V, ldv, r_out, eps_out, blocks_out);
+  return fail(SVT_ERR_ARG, "r4svd: unknown precision");
+}
+
+extern "C" svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                                   const int32_t* cols, const void* vals, double tau, double delta,
+                                   double tol, int32_t maxit, const svt_options* opt, double* U,
+                                   double* S, double* V, int32_t cap, svt_result* res,
+                                   svt_iter_log* log, int32_t log_cap) {
+  using namespace svt;
+  if (!res) return fail(SVT_ERR_ARG, "complete: null result");
+  memset(res, 0, sizeof(*res));
+  res->status = SVT_ERR_ARG;
+  if (!opt) return fail(SVT_ERR_ARG, "complete: null options");
+  if (m <= 0 || n <= 0 || nnz < 0 || maxit < 0 || cap < 1)
+    return fail(SVT_ERR_ARG, "complete: need m, n > 0, nnz >= 0, maxit >= 0, cap >= 1");
+  if (!(tau > 0.0) || !(delta > 0.0) || !std::isfinite(tau) || !std::isfinite(delta) || std::isnan(tol))
+    return fail(SVT_ERR_ARG, "complete: need finite tau > 0, delta > 0");
+  if (nnz > 0 && (!rows || !cols || !vals)) return fail(SVT_ERR_ARG, "complete: null input array");
+  svt_status st;
+  if (opt->precision == SVT_FP64)
+    st = complete_impl<double>(m, n, nnz, rows, cols, (const double*)vals, tau, delta, tol, maxit,
+                               opt, U, S, V, cap, res, log, log_cap);
+  else if (opt->precision == SVT_MIXED_FP32)
+    st = complete_impl<float>(m, n, nnz, rows, cols, (const float*)vals, tau, delta, tol, maxit,
+                              opt, U, S, V, cap, res, log, log_cap);
+  else
+    st = fail(SVT_ERR_ARG, "complete: unknown precision");
+  if (st < 0) {
+    cudaStreamSynchronize((cudaStream_t)opt->stream);
+    res->status = st;
+  }
+  return st;
+}

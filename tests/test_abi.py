@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads, and exports what the header declares.
+
+No compute call is made here (these tests run without a GPU)."""
+import ctypes as C
+
+import pytest
+
+from paper_1704_05528_gb300 import _lib as L
+from paper_1704_05528_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def test_header_declares_the_boundary():
+    names = L.header_functions()
+    for required in ("svt_complete", "svt_r4svd", "svt_pattern_create", "svt_pattern_destroy",
+                     "svt_spmm", "svt_sampled_update", "svt_gaussian_block"):
+        assert required in names
+
+
+def test_every_header_symbol_is_exported(lib):
+    names = L.header_functions()
+    assert names, "no functions parsed from the header"
+    missing = [nm for nm in names if not hasattr(lib, nm)]
+    assert not missing, f"symbols declared but not exported: {missing}"
+    assert set(names) <= set(L.SIGNATURES), "binding lacks a signature for a header function"
+
+
+def test_struct_layouts():
+    # int32 fields first, then 8-byte fields, as declared in the header
+    assert C.sizeof(L.Options) == 6 * 4 + 3 * 8 + 8
+    assert C.sizeof(L.IterLog) == 6 * 4 + 6 * 8
+    assert C.sizeof(L.Result) == 6 * 4 + 6 * 8
+
+
+def test_defaults_and_strings(lib):
+    o = L.Options()
+    lib.svt_default_options(C.byref(o))
+    assert (o.t, o.dt, o.n_power, o.r_max) == (-1, 10, 0, 0)
+    assert abs(o.beta - 0.95) < 1e-15 and o.precision == L.SVT_FP64
+    assert lib.svt_abi_version() == 1
+    assert lib.svt_status_string(L.SVT_ERR_DUPLICATE) == b"duplicate observed entry"
+    assert lib.svt_status_string(12345) == b"unknown status"
+
+
+def test_argument_validation_without_gpu(lib):
+    o = L.Options()
+    lib.svt_default_options(C.byref(o))
+    res = L.Result()
+    st = lib.svt_complete(0, 5, 0, None, None, None, 1.0, 1.0, 1e-3, 10, C.byref(o), None, None,
+                          None, 5, C.byref(res), None, 0)
+    assert st == L.SVT_ERR_ARG and res.status == L.SVT_ERR_ARG
+    st = lib.svt_complete(4, 5, 0, None, None, None, -1.0, 1.0, 1e-3, 10, C.byref(o), None, None,
+                          None, 5, C.byref(res), None, 0)
+    assert st == L.SVT_ERR_ARG
+    assert b"tau" in lib.svt_last_error()
+    h = C.c_void_p()
+    assert lib.svt_pattern_create(-1, 3, 0, None, None, None, C.byref(h)) == L.SVT_ERR_ARG
