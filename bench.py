@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of fast SVT with R4SVD on GB300.
+
+A step is one complete solve (Algorithm 4: pattern build, initialisation, then SVT
+iterations with R4SVD until the residual is below tol or maxit) on one synthetic
+workload whose inputs are already resident in device memory.  The reported metric is
+SVT iterations per second over the K timed steps (whole job: all ranks' iterations
+over the slowest rank's time); each rank solves an independent replica.
+
+Extra keys: time_to_tol_s (mean solve time when the solve converges, else null),
+a binary64 comparison leg, e2e (the same metric through the C ABI with host buffers,
+copies inside the timed region), roofline of the dominant kernel class (live CUDA
+event timings and algorithmic bytes), the CPU oracle timed on the host cores, and the
+SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle (the only other implementation of this method
+here) on a bounded sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SVT iterations/s (fast SVT with R4SVD)"
+UNIT = "iter/s"
+HBM_KERNELS = {"spmm_csr", "spmm_csc", "spmm_csc_recycled", "sampled_update", "gather_csc",
+               "init_power", "lift_U", "lift_V", "gram_B", "orthogonalise", "cholqr"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ratings71567")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--maxit", type=int, default=None)
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name, seed_offset=0):
+    import workloads
+    fn = workloads.WORKLOADS[name]
+    import inspect
+    sig = inspect.signature(fn)
+    seed = sig.parameters["seed"].default + seed_offset
+    return fn(seed=seed)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples (every 200 ms) during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ helpers
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def load_traffic(kernel):
+    """dram bytes per launch from a committed ncu capture, if the kernel is unchanged."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1704_05528_gb300", "csrc", e["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return e["bytes_per_launch"] if h == e.get("source_sha256_16") else None
+
+
+def flush_l2(buf):
+    buf.fill_(1.0)  # 256 MiB write > 129 MiB L2
+
+
+def oracle_sample(name, iters):
+    """CPU oracle on the first `iters` SVT iterations of the workload (run in a child
+    process with its thread count fixed by the environment)."""
+    import oracle
+    w = make_workload(name)
+    t0 = time.perf_counter()
+    res = oracle.svt(w.m, w.n, w.rows, w.cols, w.vals, w.tau, w.delta, w.tol, iters,
+                     t=w.t, dt=w.dt, n_power=w.n_power, beta=w.beta, eps_thr0=w.eps_thr0,
+                     r_max=w.r_max, seed=w.seed)
+    wall = time.perf_counter() - t0
+    it_s = [e["seconds"] for e in res.log]
+    print(json.dumps({"iters": len(it_s), "iter_seconds": it_s, "wall": wall}))
+
+
+def run_oracle_child(name, iters, threads, timeout=600):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--oracle-sample", str(iters)]
+    p = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=timeout)
+    if p.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {p.stderr[-2000:]}")
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    """The CPU oracle, one child process: a single solve of 1 + W + K iterations; the
+    first (Algorithm 2's wide block) is skipped, the next W are warm-up, and each of
+    the last K is one timed step (one SVT iteration)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    total = 1 + args.warmup + args.steps
+    d = run_oracle_child(args.workload, total, cores, timeout=1800)
+    timed = d["iter_seconds"][1 + args.warmup:]
+    value = len(timed) / sum(timed)
+    sample = (f"{args.workload}: SVT iterations {2 + args.warmup}..{total} of one oracle solve "
+              f"(one iteration per step; pattern build, initialisation and iteration 1 untimed), "
+              f"binary64 numpy/scipy")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def our_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1704_05528_gb300 as svt
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = make_workload(args.workload, seed_offset=rank)
+    maxit = args.maxit or w.maxit
+    prec = args.precision
+    vdt = torch.float32 if prec == "mixed" else torch.float64
+    rows = torch.from_numpy(w.rows).cuda()
+    cols = torch.from_numpy(w.cols).cuda()
+    vals = torch.from_numpy(w.vals).to(device="cuda", dtype=vdt)
+    kw = dict(t=w.t, dt=w.dt, n_power=w.n_power, beta=w.beta, eps_thr0=w.eps_thr0, r_max=w.r_max,
+              seed=w.seed)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve(p=prec, v=vals, mi=maxit):
+        return svt.complete(w.m, w.n, rows, cols, v, w.tau, w.delta, w.tol, mi, precision=p, log=False,
+                            **kw)
+
+    for _ in range(args.warmup):
+        solve()
+    svt.profile_reset()
+    svt.profile_enable(True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    iters, conv_times = 0, []
+    launches0 = svt.launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush_l2(flush)
+        t0 = time.perf_counter()
+        res = solve()
+        iters += res.iters
+        if res.converged:
+            conv_times.append(time.perf_counter() - t0)
+    ev1.record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    kernel_launches = svt.launch_count() - launches0
+    svt.profile_enable(False)
+    prof = svt.profile_read()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed, float(iters)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        elapsed, total_iters = float(tmax[0]), float(t[1])
+    else:
+        total_iters = float(iters)
+    value = total_iters / elapsed
+
+    # binary64 comparison leg (same workload, fewer steps)
+    fp64_leg = None
+    if prec == "mixed" and not args.no_fp64_leg:
+        vals64 = torch.from_numpy(w.vals).cuda()
+        solve("fp64", vals64)
+        barrier()
+        t0 = time.perf_counter()
+        r64 = solve("fp64", vals64)
+        torch.cuda.synchronize()
+        dt64 = time.perf_counter() - t0
+        fp64_leg = {"iters_per_s": r64.iters / dt64, "iters": r64.iters, "seconds": dt64,
+                    "converged": r64.converged}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the region)
+    rows_h = torch.from_numpy(w.rows).pin_memory()
+    cols_h = torch.from_numpy(w.cols).pin_memory()
+    vals_h = torch.from_numpy(w.vals).to(vdt).pin_memory()
+    r_cap = min(w.m, w.n, w.r_max) if w.r_max > 0 else min(w.m, w.n)
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        flush_l2(flush)
+        r = svt.complete(w.m, w.n, rows_h, cols_h, vals_h, w.tau, w.delta, w.tol, maxit, precision=prec,
+                         log=False, on_host=True, **kw)
+        e2e_iters += r.iters
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = int(w.nnz * (4 + 4 + (4 if prec == "mixed" else 8)))
+    d2h = int(8 * (w.m * r_cap + r_cap + w.n * r_cap))
+    e2e_val = e2e_iters * world / e2e_s
+
+    # roofline of the dominant kernel class
+    peaks, peak_src = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
+    roofline = None
+    if dom:
+        e = prof[dom]
+        per_launch_ms = e["ms"] / max(e["launches"], 1)
+        per_launch_bytes = e["bytes"] / max(e["launches"], 1)
+        if dom in HBM_KERNELS:
+            achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                        "traffic": load_traffic(dom), "peak_source": f"{peak_src} (hbm_gbs)",
+                        "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+        else:
+            roofline = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                        "frac": None, "traffic": None, "ms_per_launch": per_launch_ms}
+    breakdown = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                     "share": round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-12), 4),
+                     "GB/s": round(v["bytes"] / max(v["ms"], 1e-12) / 1e6, 1)}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cores = os.cpu_count() or 1
+            d = run_oracle_child(args.workload, 3, cores)
+            timed = d["iter_seconds"][1:]
+            cpu = {"value": len(timed) / sum(timed), "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{args.workload}: SVT iterations 2-3 of one oracle solve, iteration "
+                             f"time only (pattern build, initialisation, iteration 1 untimed), "
+                             f"binary64 numpy/scipy"}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {ex}"[:300]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "nnz_train": w.nnz, "r_max": w.r_max,
+                       "tau": w.tau, "delta": w.delta, "tol": w.tol, "maxit": maxit,
+                       "precision": "mixed fp32 (binary64 Gram/eigen/norms)" if prec == "mixed" else "fp64",
+                       "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) before each step",
+                       "iters_per_step": total_iters / world / args.steps},
+            "time_to_tol_s": statistics.mean(conv_times) if conv_times else None,
+            "fp64_leg": fp64_leg,
+            "gpu_launches": kernel_launches,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline,
+            "kernels": breakdown,
+            "cpu_baseline": cpu,
+            "clocks": clock_info,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.oracle_sample:
+        oracle_sample(args.workload, args.oracle_sample)
+        return 0
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -185,6 +185,19 @@ svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                         double* S, double* V, int32_t cap, svt_result* res,
                         svt_iter_log* log, int32_t log_cap);
 
+/* ------------------------------------------------------------------ profiling */
+/* Per-kernel-class timing (no counterpart in the paper; the analogue of its
+ * per-iteration timing figures).  When enabled, the solver brackets each kernel class
+ * with CUDA events on the launching stream and adds the algorithmic bytes the class
+ * must move.  svt_profile_read copies up to cap entries: names (cap x 32 chars,
+ * NUL-padded), launch counts, total milliseconds and total algorithmic bytes; it
+ * returns the number of entries.  All pointers are host pointers, any may be NULL. */
+void svt_profile_enable(int on);
+void svt_profile_reset(void);
+int svt_profile_read(int cap, char* names, int64_t* launches, double* ms, double* bytes);
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t svt_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

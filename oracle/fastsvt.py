@@ -43,6 +43,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 import math
+import time
 
 import numpy as np
 import scipy.sparse as sp
@@ -281,6 +282,7 @@ def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=
     log = []
     res = None
     for i in range(1, maxit + 1):
+        t_iter = time.perf_counter()
         Ys = _sparse(p, y)
         rs = r4svd(Ys, U_prev, eps_thr, i, t=t_eff, dt=dt, n_power=n_power, r_cap=r_cap,
                    seed=seed)
@@ -302,6 +304,7 @@ def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=
             eps_thr = beta * eps_thr
             entry["cooled"] = True
         entry["eps_min"] = eps_min
+        entry["seconds"] = time.perf_counter() - t_iter
         if keep_history:
             entry["S"] = rs.S.copy()
         log.append(entry)

@@ -15,7 +15,8 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "sampled_update",
-           "r4svd", "complete", "library", "FP64", "MIXED_FP32"]
+           "r4svd", "complete", "library", "launch_count", "profile_enable", "profile_reset", "profile_read",
+           "FP64", "MIXED_FP32"]
 
 FP64 = L.SVT_FP64
 MIXED_FP32 = L.SVT_MIXED_FP32
@@ -214,6 +215,33 @@ class Completion:
         return self.status == L.SVT_OK
 
 
+def profile_enable(on=True):
+    library().svt_profile_enable(1 if on else 0)
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(library().svt_launch_count())
+
+
+def profile_reset():
+    library().svt_profile_reset()
+
+
+def profile_read(cap=64):
+    """Per-kernel-class totals: name -> dict(launches, ms, bytes)."""
+    names = C.create_string_buffer(32 * cap)
+    launches = (C.c_int64 * cap)()
+    ms = (C.c_double * cap)()
+    nbytes = (C.c_double * cap)()
+    count = library().svt_profile_read(cap, names, launches, ms, nbytes)
+    out = {}
+    for i in range(min(count, cap)):
+        nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = dict(launches=int(launches[i]), ms=float(ms[i]), bytes=float(nbytes[i]))
+    return out
+
+
 def _log_list(buf, n):
     keys = [f[0] for f in L.IterLog._fields_]
     return [{k: getattr(buf[i], k) for k in keys} for i in range(n)]
@@ -232,7 +260,19 @@ def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", l
     dt = _vdtype(o.precision)
     r_cap = min(m, n, o.r_max) if o.r_max > 0 else min(m, n)
     host = isinstance(vals, np.ndarray) if on_host is None else on_host
-    if host:
+    if host and not isinstance(vals, np.ndarray):
+        # torch CPU tensors (e.g. pinned): pass their host pointers straight through
+        want = torch.float64 if o.precision == FP64 else torch.float32
+        assert rows.dtype == torch.int32 and cols.dtype == torch.int32 and vals.dtype == want
+        assert not (rows.is_cuda or cols.is_cuda or vals.is_cuda)
+        U = torch.zeros((m, r_cap), dtype=torch.float64).pin_memory()
+        S = torch.zeros(r_cap, dtype=torch.float64).pin_memory()
+        V = torch.zeros((n, r_cap), dtype=torch.float64).pin_memory()
+        args = [_ptr(rows.contiguous()), _ptr(cols.contiguous()), _ptr(vals.contiguous())]
+        outs = [_ptr(U), _ptr(S), _ptr(V)]
+        nnz = rows.numel()
+        keep = (rows, cols, vals)
+    elif host:
         np_dt = np.float64 if o.precision == FP64 else np.float32
         rows_h = np.ascontiguousarray(rows, dtype=np.int32)
         cols_h = np.ascontiguousarray(cols, dtype=np.int32)

@@ -56,6 +56,10 @@ SIGNATURES = {
     "svt_sampled_update": (C.c_int, [_P, C.c_int, _P, _I64, _P, _I64, _I32, _P, _P, _D, _PD, _P]),
     "svt_r4svd": (C.c_int, [_P, _P, _P, _I64, _I32, _D, _U32, C.POINTER(Options), _P, _I64, _P,
                             _P, _I64, _PI32, _PD, _PI32]),
+    "svt_profile_enable": (None, [C.c_int]),
+    "svt_profile_reset": (None, []),
+    "svt_launch_count": (C.c_int64, []),
+    "svt_profile_read": (C.c_int, [C.c_int, _P, C.POINTER(C.c_int64), _PD, _PD]),
     "svt_complete": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _D, _D, _D, _I32,
                                C.POINTER(Options), _P, _P, _P, _I32, C.POINTER(Result),
                                C.POINTER(IterLog), _I32]),

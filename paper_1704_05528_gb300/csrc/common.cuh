@@ -21,7 +21,13 @@ svt_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
     if (svt_e_ != cudaSuccess) return ::svt::cuda_fail(svt_e_, #expr, __FILE__, __LINE__); \
   } while (0)
 
-#define SVT_LAUNCH_CHECK() SVT_CUDA(cudaGetLastError())
+// Every kernel launch site is followed by this check; it also counts the launch.
+void count_launch();
+#define SVT_LAUNCH_CHECK()        \
+  do {                            \
+    ::svt::count_launch();        \
+    SVT_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define SVT_TRY(expr)                                                         \
   do {                                                                        \

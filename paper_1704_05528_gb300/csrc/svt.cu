@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -53,6 +54,9 @@ svt_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
   set_error("CUDA error '%s' in %s (%s:%d)", cudaGetErrorString(e), what, file, line);
   return SVT_ERR_CUDA;
 }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int num_sms() {
   static int cached = 0;
@@ -99,6 +103,105 @@ namespace {
 using clk = std::chrono::steady_clock;
 double seconds_since(clk::time_point t0) {
   return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+// ------------------------------------------------------------------ profiler
+// When enabled, each kernel class launched by the driver is bracketed by CUDA events
+// on the launching stream; elapsed times are folded in at the driver's sync points,
+// together with the algorithmic bytes that the class must move.
+struct ProfEntry {
+  char name[32];
+  int64_t launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+struct Pending {
+  int id;
+  cudaEvent_t a, b;
+  double bytes;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfEntry> g_prof;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_pool;
+
+int prof_id(const char* name) {
+  for (size_t i = 0; i < g_prof.size(); ++i)
+    if (strncmp(g_prof[i].name, name, sizeof(g_prof[i].name)) == 0) return (int)i;
+  ProfEntry e;
+  strncpy(e.name, name, sizeof(e.name) - 1);
+  e.name[sizeof(e.name) - 1] = 0;
+  g_prof.push_back(e);
+  return (int)g_prof.size() - 1;
+}
+
+cudaEvent_t pool_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold completed event pairs into the table (call after a stream synchronisation).
+void prof_flush() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  size_t keep = 0;
+  for (size_t i = 0; i < g_pending.size(); ++i) {
+    Pending& p = g_pending[i];
+    float ms = 0.f;
+    if (cudaEventQuery(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_prof[p.id].launches += 1;
+      g_prof[p.id].ms += ms;
+      g_prof[p.id].bytes += p.bytes;
+      g_pool.push_back(p.a);
+      g_pool.push_back(p.b);
+    } else {
+      g_pending[keep++] = p;
+    }
+  }
+  g_pending.resize(keep);
+  cudaGetLastError();
+}
+
+struct ProfScope {
+  bool on;
+  int id = -1;
+  cudaEvent_t a = nullptr;
+  double bytes;
+  cudaStream_t s;
+  ProfScope(const char* name, double b, cudaStream_t st) : on(g_prof_on), bytes(b), s(st) {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    id = prof_id(name);
+    a = pool_event();
+    cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = pool_event();
+    cudaEventRecord(b, s);
+    g_pending.push_back(Pending{id, a, b, bytes});
+  }
+};
+
+#define SVT_CAT2(a, b) a##b
+#define SVT_CAT(a, b) SVT_CAT2(a, b)
+#define SVT_PROF(name, bytes, stream) ProfScope SVT_CAT(svt_prof_, __LINE__)(name, (double)(bytes), stream)
+
+// Algorithmic bytes (what the method must move once) of the main kernel classes.
+inline double spmm_bytes(int64_t nnz, int64_t rows, int64_t cols, int w, int sv) {
+  return (double)nnz * (sv + 4) + 4.0 * (rows + 1) + (double)sv * ((double)cols * w + (double)rows * w);
+}
+inline double update_bytes(int64_t nnz, int64_t m, int64_t n, int k, int sv) {
+  return (double)nnz * (4 + 3 * sv) + 4.0 * (m + 1) + (double)sv * k * (double)(m + n);
+}
+inline double gemm_bytes(int64_t M, int p, int q, int sv, bool reads_c) {
+  return (double)sv * (double)M * (p + q + (reads_c ? q : 0));
 }
 
 constexpr double kExhaustedRel = 1e-7;
@@ -249,8 +352,13 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   cudaStream_t st = W.s;
   int r = s;
   double normB = 0.0;
+  const int sv = (int)sizeof(T);
+  const int64_t z = p->nnz;
   if (s > 0) {
-    SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, st)));
+    {
+      SVT_PROF("spmm_csc_recycled", spmm_bytes(z, n, m, s, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, st)));
+    }
     SVT_TRY(block_sumsq<T>(W, n, s, W.Bt, W.ldb, &normB));
   }
   auto eps_of = [&](double nb) { return normY2 > 0.0 ? (normY2 - nb) / normY2 : 0.0; };
@@ -260,10 +368,17 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   bool exhausted = false;
   while ((first || eps > eps_thr) && r < P.r_cap) {
     const int w = first ? std::min(P.t_eff, P.r_cap) : std::min(P.dt, P.r_cap - r);
-    SVT_TRY(launch_gaussian<T>(P.seed, iter, (uint32_t)blocks, n, w, W.Om, W.ldw, st));
+    {
+      SVT_PROF("gaussian", (double)sv * n * w, st);
+      SVT_TRY(launch_gaussian<T>(P.seed, iter, (uint32_t)blocks, n, w, W.Om, W.ldw, st));
+    }
     ++blocks;
-    SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, st)));
+    {
+      SVT_PROF("spmm_csr", spmm_bytes(z, m, n, w, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, st)));
+    }
     for (int it = 0; it < P.np; ++it) {
+      SVT_PROF("spmm_power", spmm_bytes(z, n, m, w, sv) + spmm_bytes(z, m, n, w, sv), st);
       SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, W.X, W.ldw, w, W.Z, W.ldw, st)));
       SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Z, W.ldw, w, W.X, W.ldw, st)));
     }
@@ -271,6 +386,7 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     SVT_TRY(block_sumsq<T>(W, m, w, W.X, W.ldw, &ssum, &scale));
     if (r > 0) {
       for (int pass = 0; pass < 2; ++pass) {  // X <- X - Q (Q^T X), twice
+        SVT_PROF("orthogonalise", gemm_bytes(m, r, w, sv, false) + gemm_bytes(m, r, w, sv, true), st);
         SVT_TRY((gemm_tn<T, T>(m, r, w, Q, W.ldq, W.X, W.ldw, W.Gs, w, W.part, st)));
         SVT_TRY((gemm_nn<T, T>(m, r, w, -1.0, Q, W.ldq, W.Gs, w, 1.0, W.X, W.ldw, W.X2, W.ldw, st)));
         std::swap(W.X, W.X2);
@@ -278,8 +394,11 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     }
     // Cholesky-QR, twice: X = Q' R
     SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
-    SVT_TRY((gemm_tn<T, T>(m, w, w, W.X, W.ldw, W.X, W.ldw, W.Gx, w, W.part, st)));
-    SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 0, W.flags, st));
+    {
+      SVT_PROF("cholqr", gemm_bytes(m, w, 0, sv, false), st);
+      SVT_TRY((gemm_tn<T, T>(m, w, w, W.X, W.ldw, W.X, W.ldw, W.Gx, w, W.part, st)));
+      SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 0, W.flags, st));
+    }
     double dmin = 0.0;
     unsigned fl = 0;
     SVT_CUDA(cudaMemcpyAsync(&dmin, W.dsc + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -288,14 +407,23 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
       exhausted = true;
       break;
     }
-    SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X, W.ldw, W.Rinv, w, 0.0, nullptr, 0, W.X2, W.ldw, st)));
-    SVT_TRY((gemm_tn<T, T>(m, w, w, W.X2, W.ldw, W.X2, W.ldw, W.Gx, w, W.part, st)));
-    SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 1, W.flags, st));
+    {
+      SVT_PROF("cholqr", gemm_bytes(m, w, w, sv, false) + gemm_bytes(m, w, 0, sv, false), st);
+      SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X, W.ldw, W.Rinv, w, 0.0, nullptr, 0, W.X2, W.ldw, st)));
+      SVT_TRY((gemm_tn<T, T>(m, w, w, W.X2, W.ldw, W.X2, W.ldw, W.Gx, w, W.part, st)));
+      SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 1, W.flags, st));
+    }
     SVT_TRY(read_flags(W, &fl));
     if (fl & FLAG_CHOLESKY) return fail(SVT_ERR_NUMERIC, "R4SVD: Cholesky-QR breakdown in block %d", blocks);
-    SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X2, W.ldw, W.Rinv, w, 0.0, nullptr, 0, Q + r, W.ldq, st)));
+    {
+      SVT_PROF("cholqr", gemm_bytes(m, w, w, sv, false), st);
+      SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X2, W.ldw, W.Rinv, w, 0.0, nullptr, 0, Q + r, W.ldq, st)));
+    }
     // B'^T = Y^T Q'
-    SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q + r, W.ldq, w, W.Bt + r, W.ldb, st)));
+    {
+      SVT_PROF("spmm_csc", spmm_bytes(z, n, m, w, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q + r, W.ldq, w, W.Bt + r, W.ldb, st)));
+    }
     double nb = 0.0;
     SVT_TRY(block_sumsq<T>(W, n, w, W.Bt + r, W.ldb, &nb));
     normB += nb;
@@ -307,13 +435,23 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   o->sigma.assign(r, 0.0);
   if (r == 0) return SVT_OK;
   // svt(B): eigen-decomposition of B B^T = (B^T)^T B^T
-  SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
-  SVT_TRY(sym_eig(r, W.G, r, W.lam, W.Ub, r, W.eigw, kRefineSteps, st));
+  {
+    SVT_PROF("gram_B", gemm_bytes(n, r, 0, sv, false), st);
+    SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
+  }
+  {
+    SVT_PROF("small_eig", 8.0 * 3 * r * r, st);
+    SVT_TRY(sym_eig(r, W.G, r, W.lam, W.Ub, r, W.eigw, kRefineSteps, st));
+  }
   std::vector<double> lam(r);
   SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
   // U = Q U_B (all r columns are recycled)
-  SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+  {
+    SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
+    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+  }
   SVT_CUDA(cudaStreamSynchronize(st));
+  prof_flush();
   for (int j = 0; j < r; ++j) {
     if (!std::isfinite(lam[j])) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
     o->sigma[j] = std::sqrt(std::max(lam[j], 0.0));
@@ -330,6 +468,7 @@ svt_status scaled_right(Work<T>& W, int r, int k, const std::vector<double>& coe
   k_scale_cols<T><<<(int)std::min<int64_t>(ceil_div(total, 256), 1024), 256, 0, W.s>>>(
       r, k, W.Ub, r, W.coef, W.Tsm);
   SVT_LAUNCH_CHECK();
+  SVT_PROF("lift_V", gemm_bytes(W.P.n, r, k, (int)sizeof(T), false), W.s);
   SVT_TRY((gemm_nn<T, T>(W.P.n, r, k, 1.0, W.Bt, W.ldb, W.Tsm, k, 0.0, nullptr, 0, W.Wk, W.ldk, W.s)));
   return SVT_OK;
 }
@@ -389,7 +528,10 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   }
   svt_pattern* pat = nullptr;
   const auto t_pat = clk::now();
-  SVT_TRY(build_pattern(m, n, nnz, d_rows, d_cols, st, &pat));
+  {
+    SVT_PROF("pattern_build", 2.0 * nnz * 36.0, st);
+    SVT_TRY(build_pattern(m, n, nnz, d_rows, d_cols, st, &pat));
+  }
   struct PatGuard { svt_pattern* p; ~PatGuard() { svt_pattern_destroy(p); } } pg{pat};
   res->seconds_pattern = seconds_since(t_pat);
 
@@ -454,6 +596,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
   SVT_LAUNCH_CHECK();
   for (int it = 0; it < P.power_steps; ++it) {
+    SVT_PROF("init_power", spmm_bytes(nnz, m, n, 1, (int)sizeof(T)) + spmm_bytes(nnz, n, m, 1, (int)sizeof(T)), st);
     SVT_TRY((launch_spmm_rows<T, double>(m, pat->row_ptr, pat->col_idx, a_csr, W.pv, 1, 1, W.pu, 1, st)));
     SVT_TRY((launch_spmm_rows<T, double>(n, pat->col_ptr, pat->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1, st)));
     SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
@@ -495,8 +638,11 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     for (int j = 0; j < k; ++j) coef[j] = (ro.sigma[j] - tau) / ro.sigma[j];
     SVT_TRY(scaled_right<T>(W, r, k, coef));
     SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
-    SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
-                              W.part, W.flags, st));
+    {
+      SVT_PROF("sampled_update", update_bytes(nnz, m, n, k, (int)sizeof(T)), st);
+      SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
+                                W.part, W.flags, st));
+    }
     double sums[3];
     unsigned fl = 0;
     SVT_CUDA(cudaMemcpyAsync(sums, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -521,7 +667,11 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     res->r = r;
     if (rel < tol) { status = SVT_OK; break; }
     // Y^(i+1) is already in y_csr (the update ran in the fused pass); refresh its CSC copy
-    SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
+    {
+      SVT_PROF("gather_csc", (double)nnz * (4 + 2 * sizeof(T)), st);
+      SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
+    }
+    prof_flush();
     normY2 = sums[2];
     std::swap(Qcur, Qnext);
     s = r;
@@ -547,6 +697,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   SVT_TRY(export_cols<T>(W, n, k, W.Wk, W.ldk, Vo, cap));
   if (So) SVT_CUDA(cudaMemcpyAsync(So, shrunk.data(), cap * sizeof(double), cudaMemcpyDefault, st));
   SVT_CUDA(cudaStreamSynchronize(st));
+  prof_flush();
   res->seconds_total = seconds_since(t_start);
   return status;
 }
@@ -749,3 +900,28 @@ extern "C" svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int3
   }
   return st;
 }
+
+extern "C" void svt_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(svt::g_prof_mu);
+  svt::g_prof_on = on != 0;
+}
+
+extern "C" void svt_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(svt::g_prof_mu);
+  svt::g_prof.clear();
+}
+
+extern "C" int svt_profile_read(int cap, char* names, int64_t* launches, double* ms, double* bytes) {
+  svt::prof_flush();
+  std::lock_guard<std::mutex> lk(svt::g_prof_mu);
+  const int count = (int)svt::g_prof.size();
+  for (int i = 0; i < count && i < cap; ++i) {
+    if (names) memcpy(names + 32 * i, svt::g_prof[i].name, 32);
+    if (launches) launches[i] = svt::g_prof[i].launches;
+    if (ms) ms[i] = svt::g_prof[i].ms;
+    if (bytes) bytes[i] = svt::g_prof[i].bytes;
+  }
+  return count;
+}
+
+extern "C" int64_t svt_launch_count(void) { return svt::g_launches.load(); }

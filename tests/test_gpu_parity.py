@@ -1,0 +1,341 @@
+"""CUDA path (through the C ABI) against the CPU oracle on identical seeded inputs.
+
+Bars: bit-exact for the pattern (integer work) and for the per-iteration revealed
+rank / kept count in binary64; relative 1e-9 for singular values and completed
+entries in binary64; relative Frobenius 1e-3 in mixed precision.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import fastsvt as OF
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+MIXED_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def svt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1704_05528_gb300 as svt
+    return svt
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (d if d > 0 else 1.0))
+
+
+def _coo(rng, m, n, z):
+    flat = rng.choice(m * n, size=z, replace=False)
+    return (flat // n).astype(np.int32), (flat % n).astype(np.int32)
+
+
+# --------------------------------------------------------------------- pattern
+PATTERN_KEYS = ("row_ptr", "col_idx", "csr_src", "col_ptr", "row_idx", "perm")
+
+
+def _check_pattern(svt, m, n, rows, cols):
+    P = svt.Pattern(m, n, rows, cols)
+    got = {k: v.cpu().numpy() for k, v in P.export().items()}
+    ref = oracle.build_pattern(m, n, rows, cols)
+    for k in PATTERN_KEYS:
+        assert np.array_equal(got[k], getattr(ref, k)), k
+
+
+@pytest.mark.parametrize("m,n,z", [(7, 5, 12), (1, 9, 4), (9, 1, 5), (13, 17, 0), (1, 1, 1),
+                                   (300, 200, 5000), (2049, 3, 6000), (3, 5000, 14000)])
+def test_pattern_bit_exact(svt, m, n, z):
+    rng = np.random.default_rng(m * 7 + n)
+    rows, cols = _coo(rng, m, n, z)
+    _check_pattern(svt, m, n, rows, cols)
+
+
+def test_pattern_dense_rows_and_empty_rows(svt):
+    m, n = 40, 3000
+    rows = np.concatenate([np.full(n, 5), np.full(n, 33), np.arange(0, 40, 7)]).astype(np.int32)
+    cols = np.concatenate([np.arange(n), np.arange(n)[::-1], np.arange(0, 40, 7) + 1]).astype(np.int32)
+    _check_pattern(svt, m, n, rows, cols)
+
+
+def test_pattern_errors(svt):
+    from paper_1704_05528_gb300 import _lib as L
+    for rows, cols, want in [([0, 1, 1], [0, 2, 2], L.SVT_ERR_DUPLICATE),
+                             ([0, 4], [0, 1], L.SVT_ERR_INDEX),
+                             ([0, 1], [0, -1], L.SVT_ERR_INDEX)]:
+        with pytest.raises(svt.SVTError) as e:
+            svt.Pattern(4, 4, np.array(rows, np.int32), np.array(cols, np.int32))
+        assert e.value.status == want
+
+
+# ------------------------------------------------------------------ Gaussians
+@pytest.mark.parametrize("n,w", [(1, 1), (10, 1), (1000, 10), (777, 7), (5, 64)])
+def test_gaussian_block(svt, n, w):
+    got = svt.gaussian_block(0x5EED, 3, 2, n, w).cpu().numpy()
+    ref = oracle.gaussian_block(0x5EED, 3, 2, n, w)
+    # same Philox words; Box-Muller through CUDA's and libm's log/sqrt/sin/cos
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+# ------------------------------------------------------------------------ SpMM
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed", 2e-6)])
+@pytest.mark.parametrize("width", [1, 3, 10, 33, 100, 513, 600])
+def test_spmm(svt, torch_mod, prec, tol, width):
+    rng = np.random.default_rng(width)
+    m, n = 611, 389
+    rows, cols = _coo(rng, m, n, 30000)
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    y = rng.standard_normal(ref_p.nnz)
+    dt = np.float64 if prec == "fp64" else np.float32
+    y = y.astype(dt).astype(np.float64)
+    Ys = OF._sparse(ref_p, y)
+    W = rng.standard_normal((n, width)).astype(dt)
+    W2 = rng.standard_normal((m, width)).astype(dt)
+    got = svt.spmm(P, torch_mod.from_numpy(y.astype(dt)), torch_mod.from_numpy(W), precision=prec)
+    got2 = svt.spmm(P, torch_mod.from_numpy(y.astype(dt)), torch_mod.from_numpy(W2), transpose=True,
+                    precision=prec)
+    assert _rel(got.cpu().numpy(), Ys @ W.astype(np.float64)) < tol
+    assert _rel(got2.cpu().numpy(), Ys.T @ W2.astype(np.float64)) < tol
+
+
+# ---------------------------------------------------------- sampled update
+@pytest.mark.parametrize("k", [0, 1, 10, 37])
+def test_sampled_update(svt, torch_mod, k):
+    rng = np.random.default_rng(100 + k)
+    m, n = 301, 257
+    rows, cols = _coo(rng, m, n, 9000)
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    U = rng.standard_normal((m, k))
+    Wm = rng.standard_normal((n, k))
+    a = rng.standard_normal(ref_p.nnz)
+    y0 = rng.standard_normal(ref_p.nnz)
+    delta = 1.7
+    x = oracle.sampled_product(U, np.ones(k), Wm, ref_p.csr_rows(), ref_p.col_idx)
+    d = a - x
+    y_ref = y0 + delta * d
+    y_dev = torch_mod.from_numpy(y0.copy()).cuda()
+    sums = svt.sampled_update(P, torch_mod.from_numpy(U), torch_mod.from_numpy(Wm),
+                              torch_mod.from_numpy(a), y_dev, delta)
+    assert _rel(y_dev.cpu().numpy(), y_ref) < 1e-14
+    assert math.isclose(sums[0], float(np.sum(d * d)), rel_tol=1e-12)
+    assert math.isclose(sums[1], float(np.sum(np.abs(d))), rel_tol=1e-12)
+    assert math.isclose(sums[2], float(np.sum(y_ref * y_ref)), rel_tol=1e-12)
+
+
+# ------------------------------------------------------------------------ R4SVD
+def _sigma_close(got, ref, tol):
+    got = np.asarray(got)
+    assert got.shape == ref.shape
+    return float(np.max(np.abs(got - ref)) / ref[0]) < tol
+
+
+@pytest.mark.parametrize("eps_thr,n_power", [(0.9, 0), (0.5, 0), (0.6, 1)])
+def test_r4svd_parity(svt, torch_mod, eps_thr, n_power):
+    w = workloads.small_lowrank()
+    ref_p = oracle.build_pattern(w.m, w.n, w.rows, w.cols)
+    P = svt.Pattern(w.m, w.n, w.rows, w.cols)
+    y = w.vals[ref_p.csr_src] * 12.0
+    Ys = OF._sparse(ref_p, y)
+    kw = dict(t=25, dt=10, n_power=n_power)
+    ro = oracle.r4svd(Ys, None, eps_thr, 1, r_cap=500, seed=w.seed, **kw)
+    rg = svt.r4svd(P, torch_mod.from_numpy(y), eps_thr, 1, seed=w.seed, **kw)
+    assert (rg["r"], rg["blocks"]) == (ro.r, ro.blocks)
+    assert abs(rg["eps"] - ro.eps) < 1e-12
+    assert _sigma_close(rg["S"].cpu().numpy(), ro.S, FP64_TOL)
+    # recycled call (Algorithm 3) from each side's own basis
+    ro2 = oracle.r4svd(Ys, ro.U, eps_thr * 0.5, 2, r_cap=500, seed=w.seed, **kw)
+    rg2 = svt.r4svd(P, torch_mod.from_numpy(y), eps_thr * 0.5, 2, U_prev=rg["U"], seed=w.seed, **kw)
+    assert (rg2["r"], rg2["blocks"]) == (ro2.r, ro2.blocks)
+    S2 = rg2["S"].cpu().numpy()
+    assert _sigma_close(S2, ro2.S, FP64_TOL)
+    k = 10  # the rank-10 part is well separated: compare the reconstruction
+    Xo = (ro2.U[:, :k] * ro2.S[:k]) @ ro2.V[:, :k].T
+    Xg = (rg2["U"][:, :k].cpu().numpy() * S2[:k]) @ rg2["V"][:, :k].cpu().numpy().T
+    assert _rel(Xg, Xo) < FP64_TOL
+
+
+def test_r4svd_exhausted_range(svt, torch_mod):
+    """A rank-3 matrix with a full pattern and a threshold no error percentage can meet:
+    the block after the first finds the range exhausted and is discarded."""
+    rng = np.random.default_rng(5)
+    m, n = 40, 30
+    M = rng.standard_normal((m, 3)) @ rng.standard_normal((3, n))
+    rows, cols = np.nonzero(np.ones((m, n)))
+    rows, cols = rows.astype(np.int32), cols.astype(np.int32)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    y = M[ref_p.csr_rows(), ref_p.col_idx]
+    ro = oracle.r4svd(OF._sparse(ref_p, y), None, -1.0, 1, t=3, dt=2, n_power=0, r_cap=30, seed=2)
+    P = svt.Pattern(m, n, rows, cols)
+    rg = svt.r4svd(P, torch_mod.from_numpy(y), -1.0, 1, t=3, dt=2, seed=2)
+    assert ro.exhausted and ro.r == 3 and rg["r"] == 3 and rg["blocks"] == ro.blocks
+    assert _sigma_close(rg["S"].cpu().numpy(), ro.S, FP64_TOL)
+
+
+# ---------------------------------------------------------------- fast SVT
+def _run_pair(svt, torch_mod, w, maxit, prec, tol=None, **over):
+    kw = dict(t=w.t, dt=w.dt, beta=w.beta, eps_thr0=w.eps_thr0, r_max=w.r_max, seed=w.seed,
+              n_power=w.n_power)
+    kw.update(over)
+    tol = w.tol if tol is None else tol
+    ref = oracle.svt(w.m, w.n, w.rows, w.cols, w.vals, w.tau, w.delta, tol, maxit, **kw)
+    vals = w.vals if prec == "fp64" else w.vals.astype(np.float32)
+    got = svt.complete(w.m, w.n, torch_mod.from_numpy(w.rows).cuda(), torch_mod.from_numpy(w.cols).cuda(),
+                       torch_mod.from_numpy(vals).cuda(), w.tau, w.delta, tol, maxit, precision=prec, **kw)
+    return ref, got
+
+
+def _completed(res_U, res_S, res_V, rows, cols):
+    to = lambda t: t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+    return oracle.sampled_product(to(res_U), to(res_S), to(res_V), rows, cols)
+
+
+def _assert_fp64_parity(w, ref, got):
+    assert got.iters == ref.iters and got.k == ref.k and got.k0 == ref.k0
+    assert [e["r"] for e in got.log] == [e["r"] for e in ref.log]
+    assert [e["k"] for e in got.log] == [e["k"] for e in ref.log]
+    assert [e["blocks"] for e in got.log] == [e["blocks"] for e in ref.log]
+    assert [bool(e["cooled"]) for e in got.log] == [e["cooled"] for e in ref.log]
+    p = ref.pattern
+    x_obs_ref = _completed(ref.U, ref.S, ref.V, p.csr_rows(), p.col_idx)
+    x_obs_got = _completed(got.U, got.S, got.V, p.csr_rows(), p.col_idx)
+    assert _rel(x_obs_got, x_obs_ref) < FP64_TOL
+    if w.held_rows.size:
+        x_h_ref = _completed(ref.U, ref.S, ref.V, w.held_rows, w.held_cols)
+        x_h_got = _completed(got.U, got.S, got.V, w.held_rows, w.held_cols)
+        assert _rel(x_h_got, x_h_ref) < FP64_TOL
+    s_got = got.S.cpu().numpy() if hasattr(got.S, "cpu") else got.S
+    if ref.k:
+        assert np.max(np.abs(s_got - ref.S) / (ref.S + w.tau)) < FP64_TOL
+
+
+def test_complete_fp64_lowrank500(svt, torch_mod):
+    """500x500 rank-10, 20% observed: the full 200-iteration run."""
+    w = workloads.small_lowrank()
+    ref, got = _run_pair(svt, torch_mod, w, w.maxit, "fp64")
+    _assert_fp64_parity(w, ref, got)
+    assert got.status == (0 if ref.status == "ok" else 1)
+
+
+def test_complete_fp64_ratings_scaled(svt, torch_mod):
+    """Rating-matrix structure (Zipf rows, empty rows, rank cap) at 0.3 scale."""
+    w = workloads.ratings_6040(scale=0.3)
+    ref, got = _run_pair(svt, torch_mod, w, 40, "fp64")
+    _assert_fp64_parity(w, ref, got)
+
+
+def test_complete_fp64_power_iterations_and_small_blocks(svt, torch_mod):
+    w = workloads.random_lowrank(90, 70, 4, 0.35, seed=11, n_hold=300, maxit=25)
+    ref, got = _run_pair(svt, torch_mod, w, 25, "fp64", t=7, dt=3, n_power=1, eps_thr0=0.4)
+    _assert_fp64_parity(w, ref, got)
+
+
+def test_complete_converges_and_recovers(svt, torch_mod):
+    w = workloads.random_lowrank(40, 40, 2, 0.6, seed=33, tol=1e-9, maxit=1000)
+    w.eps_thr0 = 1e-12
+    ref, got = _run_pair(svt, torch_mod, w, w.maxit, "fp64")
+    assert got.status == 0 and ref.status == "ok"
+    _assert_fp64_parity(w, ref, got)
+
+
+@pytest.mark.parametrize("name,maxit,kw", [("lowrank500", 60, {}), ("ratings6040", 40, {"scale": 0.3})])
+def test_complete_mixed(svt, torch_mod, name, maxit, kw):
+    w = workloads.make(name, **kw)
+    ref, got = _run_pair(svt, torch_mod, w, maxit, "mixed")
+    p = ref.pattern
+    x_obs_ref = _completed(ref.U, ref.S, ref.V, p.csr_rows(), p.col_idx)
+    x_obs_got = _completed(got.U, got.S, got.V, p.csr_rows(), p.col_idx)
+    assert _rel(x_obs_got, x_obs_ref) < MIXED_TOL
+    x_h_ref = _completed(ref.U, ref.S, ref.V, w.held_rows, w.held_cols)
+    x_h_got = _completed(got.U, got.S, got.V, w.held_rows, w.held_cols)
+    assert _rel(x_h_got, x_h_ref) < MIXED_TOL
+
+
+def test_complete_host_buffers_match_device(svt, torch_mod):
+    """The host-pointer path (copies inside the call) gives the device path's result."""
+    w = workloads.random_lowrank(120, 90, 3, 0.3, seed=3, n_hold=100, maxit=12)
+    kw = dict(t=6, dt=5, eps_thr0=0.6, seed=w.seed)
+    host = svt.complete(w.m, w.n, w.rows, w.cols, w.vals, w.tau, w.delta, 0.0, 12, **kw)
+    dev = svt.complete(w.m, w.n, torch_mod.from_numpy(w.rows).cuda(), torch_mod.from_numpy(w.cols).cuda(),
+                       torch_mod.from_numpy(w.vals).cuda(), w.tau, w.delta, 0.0, 12, **kw)
+    assert isinstance(host.U, np.ndarray) and host.k == dev.k and host.iters == dev.iters
+    assert np.array_equal(host.U, dev.U.cpu().numpy()) and np.array_equal(host.V, dev.V.cpu().numpy())
+
+
+def test_complete_edge_cases(svt, torch_mod):
+    from paper_1704_05528_gb300 import _lib as L
+    m, n = 12, 9
+    empty = svt.complete(m, n, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0), 5.0, 1.0,
+                         1e-3, 10)
+    assert empty.status == L.SVT_OK and empty.k == 0 and empty.iters == 0
+    rng = np.random.default_rng(2)
+    rows, cols = _coo(rng, m, n, 40)
+    vals = rng.standard_normal(40)
+    none = svt.complete(m, n, rows, cols, vals, 5.0, 1.0, 1e-3, 0)
+    assert none.status == L.SVT_NOT_CONVERGED and none.iters == 0 and none.k == 0
+    zero = svt.complete(m, n, rows, cols, np.zeros(40), 5.0, 1.0, 1e-3, 10)
+    assert zero.status == L.SVT_OK and zero.k == 0
+    bad = vals.copy()
+    bad[3] = np.nan
+    with pytest.raises(svt.SVTError) as e:
+        svt.complete(m, n, rows, cols, bad, 5.0, 1.0, 1e-3, 10)
+    assert e.value.status == L.SVT_ERR_NUMERIC
+    with pytest.raises(svt.SVTError) as e:
+        svt.complete(m, n, rows, np.where(cols == cols[0], n, cols).astype(np.int32), vals, 5.0, 1.0,
+                     1e-3, 10)
+    assert e.value.status == L.SVT_ERR_INDEX
+    dup_r = np.concatenate([rows, rows[:1]])
+    dup_c = np.concatenate([cols, cols[:1]])
+    with pytest.raises(svt.SVTError) as e:
+        svt.complete(m, n, dup_r, dup_c, np.concatenate([vals, vals[:1]]), 5.0, 1.0, 1e-3, 10)
+    assert e.value.status == L.SVT_ERR_DUPLICATE
+    # tau above every singular value: X stays zero and the residual is 1
+    big = svt.complete(m, n, rows, cols, vals, 1e9, 1.0, 1e-3, 3)
+    assert big.k == 0 and abs(big.rel_residual - 1.0) < 1e-12
+
+
+# --------------------------------------------------- full size, bench configuration
+@pytest.fixture(scope="module")
+def big():
+    return workloads.ratings_71567()
+
+
+def test_full_size_pattern(svt, big):
+    _check_pattern(svt, big.m, big.n, big.rows, big.cols)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_first_iterations(svt, torch_mod, big, prec):
+    """71,567 x 10,681 with 9.0M observed entries, r_max 100: the first three
+    iterations (the initial 100-wide block, then recycled bases) against the oracle."""
+    ref, got = _run_pair(svt, torch_mod, big, 3, prec)
+    p = ref.pattern
+    rng = np.random.default_rng(0)
+    sample = rng.choice(p.nnz, size=200_000, replace=False)
+    rows_s, cols_s = p.csr_rows()[sample], p.col_idx[sample]
+    x_ref = _completed(ref.U, ref.S, ref.V, rows_s, cols_s)
+    x_got = _completed(got.U, got.S, got.V, rows_s, cols_s)
+    hs = slice(0, 100_000)
+    xh_ref = _completed(ref.U, ref.S, ref.V, big.held_rows[hs], big.held_cols[hs])
+    xh_got = _completed(got.U, got.S, got.V, big.held_rows[hs], big.held_cols[hs])
+    tol = FP64_TOL if prec == "fp64" else MIXED_TOL
+    assert _rel(x_got, x_ref) < tol and _rel(xh_got, xh_ref) < tol
+    assert got.k == ref.k
+    if prec == "fp64":
+        assert [e["r"] for e in got.log] == [e["r"] for e in ref.log]

@@ -184,21 +184,22 @@ def _waterfill_counts(weights, total, cap, floor):
 def _sample_cols_without_replacement(rng, counts, col_weights, n):
     """For each row i draw counts[i] distinct columns, successive weighted sampling.
 
-    Large rows use exponential-race keys (Efraimidis-Spirakis: the counts[i]
-    smallest Exp(1)/w_j); small rows draw with replacement and redraw duplicates.
-    Returns flat (row*n + col) int64 indices.
+    Rows with more than n/8 entries use exponential-race keys (Efraimidis-Spirakis:
+    the counts[i] smallest Exp(1)/w_j).  The other rows draw with replacement in
+    sequence and keep the first counts[i] distinct columns in draw order (the same
+    law as successive sampling without replacement); rows whose draws run short are
+    drawn again with more oversampling.  Returns flat (row*n + col) int64 indices.
     """
     m = counts.shape[0]
     p = col_weights / col_weights.sum()
     cdf = np.cumsum(p)
     cdf[-1] = 1.0
-    big = np.flatnonzero(counts > 64)
-    small = np.flatnonzero(counts <= 64)
+    big = np.flatnonzero(counts > max(n // 8, 16))
     out = []
-    # large rows: exponential race
     logw = np.log(col_weights)
-    for s in range(0, big.shape[0], 256):
-        rows = big[s:s + 256]
+    chunk = max(1, (1 << 24) // max(n, 1))
+    for s in range(0, big.shape[0], chunk):
+        rows = big[s:s + chunk]
         keys = np.log(rng.exponential(size=(rows.shape[0], n))) - logw[None, :]
         for t, i in enumerate(rows):
             c = counts[i]
@@ -207,21 +208,31 @@ def _sample_cols_without_replacement(rng, counts, col_weights, n):
             else:
                 sel = np.argpartition(keys[t], c - 1)[:c].astype(np.int64)
             out.append(i * np.int64(n) + sel)
-    # small rows: draw with replacement, redraw duplicates until every row is full
-    row_of = np.repeat(small.astype(np.int64), counts[small])
-    flat = row_of * n + np.searchsorted(cdf, rng.random(row_of.shape[0]), side="right").clip(0, n - 1)
-    while True:
-        uniq = np.unique(flat)
-        have = np.bincount((uniq // n).astype(np.int64), minlength=m)
-        short = counts[small] - have[small]
-        if short.sum() == 0:
-            flat = uniq
-            break
-        need_rows = np.repeat(small.astype(np.int64), short)
-        redraw = need_rows * n + np.searchsorted(cdf, rng.random(need_rows.shape[0]),
-                                                 side="right").clip(0, n - 1)
-        flat = np.concatenate([uniq, redraw])
-    out.append(flat)
+    todo = np.flatnonzero((counts <= max(n // 8, 16)) & (counts > 0)).astype(np.int64)
+    factor = 1.5
+    while todo.size:
+        c = counts[todo]
+        draws = np.ceil(factor * c + 8).astype(np.int64)
+        row_of = np.repeat(todo, draws)
+        col = np.searchsorted(cdf, rng.random(row_of.shape[0]), side="right").clip(0, n - 1)
+        order = np.arange(row_of.shape[0], dtype=np.int64)       # draw order (rows contiguous)
+        key = row_of * n + col
+        srt = np.lexsort((order, key))                            # by key, then draw order
+        first = np.ones(srt.shape[0], dtype=bool)
+        first[1:] = key[srt][1:] != key[srt][:-1]
+        keep = np.sort(srt[first])                                # first occurrences, draw order
+        kr = row_of[keep]
+        # rank of each kept draw within its row
+        starts = np.flatnonzero(np.r_[True, kr[1:] != kr[:-1]])
+        rank = np.arange(kr.shape[0]) - np.repeat(starts, np.diff(np.r_[starts, kr.shape[0]]))
+        need = np.zeros(m, dtype=np.int64)
+        need[todo] = c
+        have = np.bincount(kr, minlength=m)
+        full = have[todo] >= c
+        sel = keep[(rank < need[kr]) & (have[kr] >= need[kr])]
+        out.append(key[sel])
+        todo = todo[~full]
+        factor *= 2.0
     return np.concatenate(out)
 
 
