@@ -326,6 +326,7 @@ def our_arm(args):
 
     # roofline of the dominant kernel class
     peaks, peak_src = load_peaks()
+    sweeps = prof.pop("jacobi_sweeps", None)
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
     roofline = None
     if dom:
@@ -377,6 +378,7 @@ def our_arm(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
             "kernels": breakdown,
+            "jacobi_sweeps_per_call": (sweeps["bytes"] / max(sweeps["launches"], 1)) if sweeps else None,
             "cpu_baseline": cpu,
             "clocks": clock_info,
         }

@@ -123,5 +123,9 @@ struct svt_pattern {
   int32_t* row_idx = nullptr;   // nnz, CSC
   int32_t* perm = nullptr;      // nnz, CSR slot of each CSC slot
   int32_t* csr_row = nullptr;   // nnz, row of each CSR slot
+  int64_t chunk = 0;            // entries per work chunk of the entry-balanced kernels
+  int64_t nchunks = 0;
+  int32_t* chunk_row_csr = nullptr;  // first CSR row touched by each chunk
+  int32_t* chunk_row_csc = nullptr;  // first CSC column touched by each chunk
   void* block = nullptr;        // single device allocation holding the arrays
 };

@@ -4,8 +4,9 @@
 //
 // gemm_tn: C = A^T B with the long dimension M split across blocks; each block writes a
 //          binary64 partial tile and a second pass sums the partials in split order, so
-//          the result does not depend on scheduling.  Products of binary32 inputs are
-//          formed in binary64 (exact), which keeps the Gram matrices binary64-accurate.
+//          the result does not depend on scheduling.  Binary32 inputs are accumulated
+//          with error-free products and TwoSum in binary32 pairs (binary64-accurate at
+//          binary32 speed); a Gram matrix (A == B) computes its upper tiles only.
 // gemm_nn: C = alpha A B + beta Cin, A tall (M x p), B small binary64 (p x q), tiled
 //          64 x 32 per block through shared memory.
 // chol_inv: one-block Cholesky G = R^T R of a small SPD matrix and R^-1.
@@ -22,55 +23,83 @@ namespace {
 
 constexpr int TN_TILE = 32;
 
+// Error-free accumulation in binary32 pairs: the product p = a*b is rounded and its error
+// e = fma(a, b, -p) is exact; p enters hi by Knuth's TwoSum (exact), the two errors
+// gather in lo.  hi + lo tracks the sum to about 2^-44 relative, at binary32 speed.
+__device__ __forceinline__ void dd_fma(float a, float b, float& hi, float& lo) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = hi + p;
+  const float z = t - hi;
+  const float err = (hi - (t - z)) + (p - z);
+  hi = t;
+  lo += err + e;
+}
+
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(256)
 k_gemm_tn_part(int64_t M, int p, int q, const TA* __restrict__ A, int64_t lda,
                const TB* __restrict__ B, int64_t ldb, int64_t rows_per_split,
-               double* __restrict__ part) {
-  __shared__ double As[TN_TILE][TN_TILE + 1];
-  __shared__ double Bs[TN_TILE][TN_TILE + 1];
+               double* __restrict__ part, int symmetric) {
+  if (symmetric && blockIdx.x > blockIdx.y) return;   // lower tiles mirror upper ones
+  constexpr bool kF32 = sizeof(TA) == 4 && sizeof(TB) == 4;
+  using TS = typename std::conditional<kF32, float, double>::type;
+  __shared__ TS As[TN_TILE][TN_TILE + 1];
+  __shared__ TS Bs[TN_TILE][TN_TILE + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int a0 = blockIdx.x * TN_TILE, b0 = blockIdx.y * TN_TILE;
   const int64_t i_beg = (int64_t)blockIdx.z * rows_per_split;
   int64_t i_end = i_beg + rows_per_split;
   if (i_end > M) i_end = M;
-  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  TS acc[4] = {TS(0), TS(0), TS(0), TS(0)};
+  TS lo[4] = {TS(0), TS(0), TS(0), TS(0)};
   for (int64_t i0 = i_beg; i0 < i_end; i0 += TN_TILE) {
     for (int t = threadIdx.x; t < TN_TILE * TN_TILE; t += blockDim.x) {
       const int rr = t / TN_TILE, cc = t % TN_TILE;
       const int64_t i = i0 + rr;
       const bool in = i < i_end;
-      As[rr][cc] = (in && a0 + cc < p) ? (double)A[i * lda + a0 + cc] : 0.0;
-      Bs[rr][cc] = (in && b0 + cc < q) ? (double)B[i * ldb + b0 + cc] : 0.0;
+      As[rr][cc] = (in && a0 + cc < p) ? (TS)A[i * lda + a0 + cc] : TS(0);
+      Bs[rr][cc] = (in && b0 + cc < q) ? (TS)B[i * ldb + b0 + cc] : TS(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < TN_TILE; ++kk) {
-      const double x0 = As[kk][ty], x1 = As[kk][ty + 16];
-      const double y0 = Bs[kk][tx], y1 = Bs[kk][tx + 16];
-      acc00 = fma(x0, y0, acc00);
-      acc01 = fma(x0, y1, acc01);
-      acc10 = fma(x1, y0, acc10);
-      acc11 = fma(x1, y1, acc11);
+      const TS x0 = As[kk][ty], x1 = As[kk][ty + 16];
+      const TS y0 = Bs[kk][tx], y1 = Bs[kk][tx + 16];
+      if constexpr (kF32) {
+        dd_fma(x0, y0, acc[0], lo[0]);
+        dd_fma(x0, y1, acc[1], lo[1]);
+        dd_fma(x1, y0, acc[2], lo[2]);
+        dd_fma(x1, y1, acc[3], lo[3]);
+      } else {
+        acc[0] = fma(x0, y0, acc[0]);
+        acc[1] = fma(x0, y1, acc[1]);
+        acc[2] = fma(x1, y0, acc[2]);
+        acc[3] = fma(x1, y1, acc[3]);
+      }
     }
     __syncthreads();
   }
   double* P = part + (int64_t)blockIdx.z * p * q;
   const int a_0 = a0 + ty, a_1 = a0 + ty + 16, b_0 = b0 + tx, b_1 = b0 + tx + 16;
-  if (a_0 < p && b_0 < q) P[(int64_t)a_0 * q + b_0] = acc00;
-  if (a_0 < p && b_1 < q) P[(int64_t)a_0 * q + b_1] = acc01;
-  if (a_1 < p && b_0 < q) P[(int64_t)a_1 * q + b_0] = acc10;
-  if (a_1 < p && b_1 < q) P[(int64_t)a_1 * q + b_1] = acc11;
+  if (a_0 < p && b_0 < q) P[(int64_t)a_0 * q + b_0] = (double)acc[0] + (double)lo[0];
+  if (a_0 < p && b_1 < q) P[(int64_t)a_0 * q + b_1] = (double)acc[1] + (double)lo[1];
+  if (a_1 < p && b_0 < q) P[(int64_t)a_1 * q + b_0] = (double)acc[2] + (double)lo[2];
+  if (a_1 < p && b_1 < q) P[(int64_t)a_1 * q + b_1] = (double)acc[3] + (double)lo[3];
 }
 
+// C[a][b] = sum_z part[z][a][b]; for a symmetric product the lower tiles read the
+// mirrored upper entry.
 __global__ void k_reduce_parts(int p, int q, int splits, const double* __restrict__ part,
-                               double* __restrict__ C, int64_t ldc) {
+                               double* __restrict__ C, int64_t ldc, int symmetric) {
   const int64_t pq = (int64_t)p * q;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pq;
        t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t / q, b = t % q;
+    const int64_t src = (symmetric && (a / TN_TILE) > (b / TN_TILE)) ? b * q + a : t;
     double s = 0.0;
-    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * pq + t];
-    C[(t / q) * ldc + (t % q)] = s;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * pq + src];
+    C[a * ldc + b] = s;
   }
 }
 
@@ -248,9 +277,10 @@ svt_status gemm_tn(int64_t M, int p, int q, const TA* A, int64_t lda, const TB* 
   const int64_t rows = round_up(ceil_div(M, splits), TN_TILE);
   const int used = (int)ceil_div(M, rows);
   dim3 grid((unsigned)ceil_div(p, TN_TILE), (unsigned)ceil_div(q, TN_TILE), (unsigned)used);
-  k_gemm_tn_part<TA, TB><<<grid, 256, 0, s>>>(M, p, q, A, lda, B, ldb, rows, part);
+  const int sym = (A == (const TA*)(const void*)B && p == q && lda == ldb) ? 1 : 0;
+  k_gemm_tn_part<TA, TB><<<grid, 256, 0, s>>>(M, p, q, A, lda, B, ldb, rows, part, sym);
   SVT_LAUNCH_CHECK();
-  k_reduce_parts<<<grid_cap((int64_t)p * q, 256, 8), 256, 0, s>>>(p, q, used, part, C, ldc);
+  k_reduce_parts<<<grid_cap((int64_t)p * q, 256, 8), 256, 0, s>>>(p, q, used, part, C, ldc, sym);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -291,7 +321,7 @@ svt_status colsumsq(int64_t M, int w, const T* X, int64_t ldx, double* sums, dou
   const int blocks = (int)ceil_div(M > 0 ? M : 1, rows);
   k_colsumsq_part<T><<<blocks, 256, 0, s>>>(M, w, X, ldx, rows, part);
   SVT_LAUNCH_CHECK();
-  k_reduce_parts<<<grid_cap(w, 256, 8), 256, 0, s>>>(1, w, blocks, part, sums, w);
+  k_reduce_parts<<<grid_cap(w, 256, 8), 256, 0, s>>>(1, w, blocks, part, sums, w, 0);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }

@@ -19,11 +19,16 @@ svt_status launch_gaussian(uint64_t seed, uint32_t iter, uint32_t blk, int64_t n
                            int64_t ld, cudaStream_t s);
 
 // spmm.cu ---------------------------------------------------------------------
-// out[r, 0:w] = sum_{e in ptr[r]..ptr[r+1]} val[e] * W[idx[e], 0:w] for r < nrows.
+// out[r, 0:w] = sum_{e in ptr[r]..ptr[r+1]} val[e] * W[idx[e], 0:w] for r < nrows, with
+// the nnz entries split into equal chunks; `scratch` holds spmm_scratch_bytes(nnz, w,
+// sizeof(TD)) bytes.
+int64_t chunk_size(int64_t nnz);
+size_t spmm_scratch_bytes(int64_t nnz, int w, int elem);
 template <typename TV, typename TD>
 svt_status launch_spmm_rows(int64_t nrows, const int32_t* ptr, const int32_t* idx,
                             const TV* val, const TD* W, int64_t ldw, int w, TD* out,
-                            int64_t ldo, cudaStream_t s);
+                            int64_t ldo, void* scratch, int64_t nnz, cudaStream_t s,
+                            const int32_t* chunk_row = nullptr);
 // dst[q] = src[perm[q]]
 template <typename T>
 svt_status launch_gather(int64_t count, const int32_t* perm, const T* src, T* dst,
@@ -62,6 +67,12 @@ size_t eig_scratch(int r);
 // start, then binary64 refinement steps built from GEMMs.
 svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
                    double* work, int refine_steps, cudaStream_t s);
+// The two stages of sym_eig: binary32 Jacobi start (eigenvectors in work), then the
+// binary64 refinement and the sort.
+svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
+                     int* sweeps_out);
+svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
+                      double* work, int refine_steps, cudaStream_t s);
 
 // update.cu -------------------------------------------------------------------
 size_t reduce_scratch();

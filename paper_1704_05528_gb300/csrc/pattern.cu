@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace svt {
 namespace {
@@ -172,6 +173,23 @@ __global__ void k_offsets(int64_t nnz, const int32_t* __restrict__ major, int64_
   }
 }
 
+// First compressed row touched by each chunk of C entries: the smallest r with
+// ptr[r] >= beg if ptr[r] == beg (rows that start exactly at the chunk, possibly empty,
+// belong to it), else the row that covers beg.
+__global__ void k_chunk_rows(int64_t nrows, int64_t C, int64_t nchunks, const int32_t* __restrict__ ptr,
+                             int32_t* __restrict__ out) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t beg = c * C;
+    int64_t lo = 0, hi = nrows + 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ptr[mid] < beg) lo = mid + 1; else hi = mid;
+    }
+    out[c] = (int32_t)((lo > nrows || ptr[lo] > beg) ? lo - 1 : lo);
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   const int64_t g = ceil_div(n > 0 ? n : 1, threads);
   const int64_t cap = (int64_t)num_sms() * 16;
@@ -227,6 +245,10 @@ svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     p.row_idx = ar.take<int32_t>(nnz);
     p.perm = ar.take<int32_t>(nnz);
     p.csr_row = ar.take<int32_t>(nnz);
+    p.chunk = chunk_size(nnz > 0 ? nnz : 1);
+    p.nchunks = ceil_div(nnz, p.chunk);
+    p.chunk_row_csr = ar.take<int32_t>(p.nchunks);
+    p.chunk_row_csc = ar.take<int32_t>(p.nchunks);
   };
   svt_pattern probe;
   layout(a, probe);
@@ -299,6 +321,12 @@ svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     SVT_CUDA(cudaMemcpyAsync(p->perm, vals[res], nnz * sizeof(int32_t),
                              cudaMemcpyDeviceToDevice, s));
     k_offsets<<<grid_for(n + 1, 256), 256, 0, s>>>(nnz, col_of, n, p->col_ptr);
+    SVT_LAUNCH_CHECK();
+    k_chunk_rows<<<grid_for(p->nchunks, 256), 256, 0, s>>>(m, p->chunk, p->nchunks, p->row_ptr,
+                                                          p->chunk_row_csr);
+    SVT_LAUNCH_CHECK();
+    k_chunk_rows<<<grid_for(p->nchunks, 256), 256, 0, s>>>(n, p->chunk, p->nchunks, p->col_ptr,
+                                                          p->chunk_row_csc);
     SVT_LAUNCH_CHECK();
     SVT_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SVT_CUDA(cudaStreamSynchronize(s));

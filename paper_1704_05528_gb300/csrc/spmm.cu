@@ -1,12 +1,15 @@
 // Sparse (Y on Lambda) times tall-skinny dense block: the matrix-block products that
 // dominate Algorithms 1-3 (O((np+2) r T_mult), Section 2.2).
 //
-// One warp per compressed row (a row of Y in CSR order for Y W, a column of Y in CSC
-// order for Y^T W).  The warp is split into 32/G groups of G lanes; each group walks
-// every (32/G)-th entry of the row and its lanes cover the block's columns
-// (lane, lane + G, ...), so one gathered row of W is read with consecutive lanes.
-// The groups' partial sums are combined by a fixed xor-shuffle tree, so results are
-// reproducible run to run.
+// Work is split by entries, not by rows: warp c owns entries [c*C, (c+1)*C) of the
+// compressed order, so a column with 60k entries costs the same as 60k scattered
+// entries; each chunk's first row is precomputed with the pattern.  Inside a warp,
+// groups of G lanes each take one entry at a time and gather its row of W with 16-byte
+// vector loads (lane l of a group holds vectors l, l+G, ...).
+// A row lying entirely inside a chunk is written directly; a row crossing chunk
+// boundaries leaves one partial per chunk (the chunk's first row in slot "head", its
+// last row in slot "tail"), and a fix-up pass adds them in chunk order.  The result is
+// therefore independent of scheduling.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -17,42 +20,125 @@
 namespace svt {
 namespace {
 
-template <typename TV, typename TD, int G, int MAXC>
+template <typename T, int VEC> struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<double, 2> { using type = double2; };
+template <typename T> struct VecT<T, 1> { using type = T; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ void load_vec(const T* p, T (&v)[VEC]) {
+  if constexpr (VEC == 1) {
+    v[0] = p[0];
+  } else if constexpr (VEC == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+}
+
+// First row of the chunk starting at entry `beg`: rows with ptr[r] == beg (possibly empty)
+// belong to this chunk; a row that started earlier and covers `beg` comes first.
+__device__ __forceinline__ int64_t chunk_first_row(const int32_t* __restrict__ ptr, int64_t nrows,
+                                                   int64_t beg) {
+  int64_t lo = 0, hi = nrows + 1;  // smallest r in [0, nrows] with ptr[r] >= beg
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ptr[mid] < beg) lo = mid + 1; else hi = mid;
+  }
+  if (lo > nrows || ptr[lo] > beg) return lo - 1;
+  return lo;
+}
+
+template <typename TV, typename TD, int VEC, int G, int MAXV>
 __global__ void __launch_bounds__(256)
-k_spmm_rows(int64_t nrows, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-            const TV* __restrict__ val, const TD* __restrict__ W, int64_t ldw, int w,
-            TD* __restrict__ out, int64_t ldo) {
+k_spmm_chunked(int64_t nrows, int64_t nnz, int64_t C, const int32_t* __restrict__ ptr,
+               const int32_t* __restrict__ idx, const TV* __restrict__ val, const TD* __restrict__ W,
+               int64_t ldw, int w, TD* __restrict__ out, int64_t ldo, TD* __restrict__ part,
+               int64_t ldp, int32_t* __restrict__ tail_row, int64_t nchunks,
+               const int32_t* __restrict__ chunk_row) {
   constexpr int NG = 32 / G;
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane % G;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = wid; row < nrows; row += nw) {
-    TD acc[MAXC];
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (chunk >= nchunks) return;
+  const int64_t beg = chunk * C;
+  const int64_t end = (beg + C < nnz) ? beg + C : nnz;
+  const bool last_chunk = (chunk == nchunks - 1);
+  int64_t r = chunk_row ? chunk_row[chunk] : chunk_first_row(ptr, nrows, beg);
+  int32_t my_tail = -1;
+  for (; r < nrows; ++r) {
+    const int64_t rb = ptr[r], re = ptr[r + 1];
+    if (rb >= end && !(last_chunk && rb == nnz)) break;
+    const int64_t sb = rb > beg ? rb : beg;
+    const int64_t se = re < end ? re : end;
+    TD acc[MAXV][VEC];
 #pragma unroll
-    for (int t = 0; t < MAXC; ++t) acc[t] = TD(0);
-    const int beg = ptr[row], end = ptr[row + 1];
-    for (int e = beg + grp; e < end; e += NG) {
+    for (int a = 0; a < MAXV; ++a)
+#pragma unroll
+      for (int b = 0; b < VEC; ++b) acc[a][b] = TD(0);
+    for (int64_t e = sb + grp; e < se; e += NG) {
       const TD v = (TD)val[e];
       const TD* wr = W + (int64_t)idx[e] * ldw;
 #pragma unroll
-      for (int t = 0; t < MAXC; ++t) {
-        const int col = gl + t * G;
-        if (col < w) acc[t] = fma(v, wr[col], acc[t]);
+      for (int a = 0; a < MAXV; ++a) {
+        const int c0 = (gl + a * G) * VEC;
+        if (c0 < w) {
+          TD x[VEC];
+          load_vec<TD, VEC>(wr + c0, x);
+#pragma unroll
+          for (int b = 0; b < VEC; ++b) acc[a][b] = fma(v, x[b], acc[a][b]);
+        }
       }
     }
 #pragma unroll
-    for (int t = 0; t < MAXC; ++t) {
+    for (int a = 0; a < MAXV; ++a)
 #pragma unroll
-      for (int o = G; o < 32; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+      for (int b = 0; b < VEC; ++b)
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1) acc[a][b] += __shfl_xor_sync(0xffffffffu, acc[a][b], o);
+    const bool starts_before = rb < beg;
+    const bool ends_after = re > end;
+    TD* dst;
+    if (!starts_before && !ends_after) {
+      dst = out + r * ldo;
+    } else if (starts_before) {
+      dst = part + (2 * chunk) * ldp;         // head slot
+    } else {
+      dst = part + (2 * chunk + 1) * ldp;     // tail slot
+      my_tail = (int32_t)r;
     }
     if (grp == 0) {
 #pragma unroll
-      for (int t = 0; t < MAXC; ++t) {
-        const int col = gl + t * G;
-        if (col < w) out[row * ldo + col] = acc[t];
+      for (int a = 0; a < MAXV; ++a) {
+        const int c0 = (gl + a * G) * VEC;
+#pragma unroll
+        for (int b = 0; b < VEC; ++b)
+          if (c0 + b < w) dst[c0 + b] = acc[a][b];
       }
     }
+  }
+  if (lane == 0) tail_row[chunk] = my_tail;
+}
+
+// out[r] = tail(c) + head(c+1) + ... + head(c_last) for the row r left in chunk c's tail;
+// one warp per chunk, lanes over columns.
+template <typename TD>
+__global__ void __launch_bounds__(256)
+k_spmm_fixup(int64_t nchunks, int64_t C, const int32_t* __restrict__ ptr,
+             const TD* __restrict__ part, int64_t ldp, const int32_t* __restrict__ tail_row, int w,
+             TD* __restrict__ out, int64_t ldo) {
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (chunk >= nchunks) return;
+  const int32_t r = tail_row[chunk];
+  if (r < 0) return;
+  const int64_t c_last = ((int64_t)ptr[r + 1] - 1) / C;
+  for (int c = lane; c < w; c += 32) {
+    TD s = part[(2 * chunk + 1) * ldp + c];
+    for (int64_t k = chunk + 1; k <= c_last; ++k) s += part[(2 * k) * ldp + c];
+    out[(int64_t)r * ldo + c] = s;
   }
 }
 
@@ -64,40 +150,104 @@ __global__ void k_gather(int64_t count, const int32_t* __restrict__ perm, const 
     dst[q] = src[perm[q]];
 }
 
-template <typename TV, typename TD, int G, int MAXC>
-svt_status run_spmm(int64_t nrows, const int32_t* ptr, const int32_t* idx, const TV* val,
-                    const TD* W, int64_t ldw, int w, TD* out, int64_t ldo, cudaStream_t s) {
-  const int64_t warps_wanted = nrows;
-  const int64_t warps_cap = (int64_t)num_sms() * 64;
-  const int64_t warps = warps_wanted < warps_cap ? warps_wanted : warps_cap;
-  const int blocks = (int)ceil_div(warps, 8);
-  k_spmm_rows<TV, TD, G, MAXC><<<blocks, 256, 0, s>>>(nrows, ptr, idx, val, W, ldw, w, out, ldo);
-  SVT_LAUNCH_CHECK();
-  return SVT_OK;
+__global__ void k_zero_rows(int64_t nrows, int w, void* out_, int64_t ldo, int elem) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrows * w;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / w;
+    const int j = (int)(t - i * w);
+    if (elem == 8) reinterpret_cast<double*>(out_)[i * ldo + j] = 0.0;
+    else reinterpret_cast<float*>(out_)[i * ldo + j] = 0.0f;
+  }
 }
 
 }  // namespace
 
+int64_t chunk_size(int64_t nnz) {
+  int64_t c = ceil_div(nnz, (int64_t)num_sms() * 256);
+  c = round_up(c < 32 ? 32 : c, 32);
+  return c > 4096 ? 4096 : c;
+}
+
+namespace {
+
+template <typename TV, typename TD, int VEC, int G, int MAXV>
+svt_status run_chunked(int64_t nrows, int64_t nnz, const int32_t* ptr, const int32_t* idx,
+                       const TV* val, const TD* W, int64_t ldw, int w, TD* out, int64_t ldo,
+                       TD* part, int32_t* tails, const int32_t* chunk_row, cudaStream_t s) {
+  const int64_t C = chunk_size(nnz);
+  const int64_t nchunks = ceil_div(nnz, C);
+  const int64_t ldp = round_up(w, 4);
+  const int blocks = (int)ceil_div(nchunks, 8);
+  k_spmm_chunked<TV, TD, VEC, G, MAXV><<<blocks, 256, 0, s>>>(nrows, nnz, C, ptr, idx, val, W, ldw, w,
+                                                              out, ldo, part, ldp, tails, nchunks,
+                                                              chunk_row);
+  SVT_LAUNCH_CHECK();
+  k_spmm_fixup<TD><<<blocks, 256, 0, s>>>(nchunks, C, ptr, part, ldp, tails, w, out, ldo);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+// Dispatch on width (in vectors of VEC elements): G lanes per entry, MAXV vectors per lane.
+template <typename TV, typename TD, int VEC>
+svt_status dispatch(int64_t nrows, int64_t nnz, const int32_t* ptr, const int32_t* idx,
+                    const TV* val, const TD* W, int64_t ldw, int w, TD* out, int64_t ldo,
+                    TD* part, int32_t* tails, const int32_t* chunk_row, cudaStream_t s) {
+  const int nv = (int)ceil_div(w, VEC);
+  // narrow blocks: one vector per lane, several entries per warp; wide blocks: one entry
+  // per warp, up to 16 vectors per lane
+#define SVT_RUN(G, MV) return run_chunked<TV, TD, VEC, G, MV>(nrows, nnz, ptr, idx, val, W, ldw, w, out, ldo, part, tails, chunk_row, s)
+  if (nv <= 1) SVT_RUN(1, 1);
+  if (nv <= 2) SVT_RUN(2, 1);
+  if (nv <= 4) SVT_RUN(4, 1);
+  if (nv <= 8) SVT_RUN(8, 1);
+  if (nv <= 16) SVT_RUN(16, 1);
+  if (nv <= 32) SVT_RUN(32, 1);
+  if (nv <= 64) SVT_RUN(32, 2);
+  if (nv <= 128) SVT_RUN(32, 4);
+  if (nv <= 256) SVT_RUN(32, 8);
+  SVT_RUN(32, 16);
+#undef SVT_RUN
+}
+
+}  // namespace
+
+// Scratch of one SpMM call: per chunk two partial rows (head, tail) of up to 512
+// columns, then one int32 per chunk naming the row left in its tail slot.
+static int64_t part_bytes(int64_t nchunks, int w, int elem) {
+  const int64_t wc = w < 512 ? w : 512;
+  return round_up(2 * nchunks * round_up(wc, 4) * elem, 256);
+}
+
+size_t spmm_scratch_bytes(int64_t nnz, int w, int elem) {
+  const int64_t nchunks = ceil_div(nnz > 0 ? nnz : 1, chunk_size(nnz > 0 ? nnz : 1));
+  return (size_t)(part_bytes(nchunks, w, elem) + nchunks * 4 + 256);
+}
+
 template <typename TV, typename TD>
 svt_status launch_spmm_rows(int64_t nrows, const int32_t* ptr, const int32_t* idx,
                             const TV* val, const TD* W, int64_t ldw, int w, TD* out,
-                            int64_t ldo, cudaStream_t s) {
+                            int64_t ldo, void* scratch, int64_t nnz, cudaStream_t s,
+                            const int32_t* chunk_row) {
   if (nrows <= 0 || w <= 0) return SVT_OK;
+  if (nnz == 0) {
+    const int64_t zb = ceil_div(nrows * w, 256);
+    k_zero_rows<<<(int)(zb < 4096 ? zb : 4096), 256, 0, s>>>(
+        nrows, w, out, ldo, (int)sizeof(TD));
+    SVT_LAUNCH_CHECK();
+    return SVT_OK;
+  }
+  const int64_t nchunks = ceil_div(nnz, chunk_size(nnz));
+  TD* part = reinterpret_cast<TD*>(scratch);
+  int32_t* tails = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(scratch) +
+                                              part_bytes(nchunks, w, (int)sizeof(TD)));
   for (int c0 = 0; c0 < w; c0 += 512) {
     const int wc = (w - c0) < 512 ? (w - c0) : 512;
     const TD* Wc = W + c0;
     TD* oc = out + c0;
-    svt_status st;
-    if (wc == 1) st = run_spmm<TV, TD, 1, 1>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc == 2) st = run_spmm<TV, TD, 2, 1>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 4) st = run_spmm<TV, TD, 4, 1>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 8) st = run_spmm<TV, TD, 8, 1>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 16) st = run_spmm<TV, TD, 16, 1>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 32) st = run_spmm<TV, TD, 32, 1>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 64) st = run_spmm<TV, TD, 32, 2>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 128) st = run_spmm<TV, TD, 32, 4>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else if (wc <= 256) st = run_spmm<TV, TD, 32, 8>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
-    else st = run_spmm<TV, TD, 32, 16>(nrows, ptr, idx, val, Wc, ldw, wc, oc, ldo, s);
+    constexpr int V = (sizeof(TD) == 4) ? 4 : 2;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(Wc) % 16) == 0) && (ldw % V == 0);
+    svt_status st = aligned ? dispatch<TV, TD, V>(nrows, nnz, ptr, idx, val, Wc, ldw, wc, oc, ldo, part, tails, chunk_row, s)
+                            : dispatch<TV, TD, 1>(nrows, nnz, ptr, idx, val, Wc, ldw, wc, oc, ldo, part, tails, chunk_row, s);
     if (st < 0) return st;
   }
   return SVT_OK;
@@ -115,15 +265,13 @@ svt_status launch_gather(int64_t count, const int32_t* perm, const T* src, T* ds
   return SVT_OK;
 }
 
-template svt_status launch_spmm_rows<double, double>(int64_t, const int32_t*, const int32_t*,
-                                                     const double*, const double*, int64_t, int,
-                                                     double*, int64_t, cudaStream_t);
-template svt_status launch_spmm_rows<float, float>(int64_t, const int32_t*, const int32_t*,
-                                                   const float*, const float*, int64_t, int,
-                                                   float*, int64_t, cudaStream_t);
-template svt_status launch_spmm_rows<float, double>(int64_t, const int32_t*, const int32_t*,
-                                                    const float*, const double*, int64_t, int,
-                                                    double*, int64_t, cudaStream_t);
+#define SVT_INST_SPMM(TV, TD)                                                                   \
+  template svt_status launch_spmm_rows<TV, TD>(int64_t, const int32_t*, const int32_t*,          \
+                                               const TV*, const TD*, int64_t, int, TD*, int64_t, \
+                                               void*, int64_t, cudaStream_t, const int32_t*);
+SVT_INST_SPMM(double, double)
+SVT_INST_SPMM(float, float)
+SVT_INST_SPMM(float, double)
 template svt_status launch_gather<double>(int64_t, const int32_t*, const double*, double*,
                                           cudaStream_t);
 template svt_status launch_gather<float>(int64_t, const int32_t*, const float*, float*,

@@ -206,7 +206,7 @@ inline double gemm_bytes(int64_t M, int p, int q, int sv, bool reads_c) {
 
 constexpr double kExhaustedRel = 1e-7;
 constexpr uint32_t kPowerSeedIter = 0xFFFFFFFFu;
-constexpr int kRefineSteps = 3;
+constexpr int kRefineSteps = 2;
 
 struct Params {
   int64_t m, n;
@@ -274,6 +274,7 @@ struct Work {
   double *coef = nullptr, *part = nullptr, *eigw = nullptr, *dsc = nullptr, *colss = nullptr;
   double *pv = nullptr, *pu = nullptr, *pw = nullptr;  // power-iteration vectors
   unsigned* flags = nullptr;
+  void* spmm_scr = nullptr;         // partial rows of the entry-chunked SpMM
 
   void layout(Arena& a) {
     const int64_t m = P.m, n = P.n, z = pat->nnz;
@@ -307,6 +308,9 @@ struct Work {
     colss = a.take<double>(std::max(wmax, rc));
     pv = a.take<double>(n); pw = a.take<double>(n); pu = a.take<double>(m);
     flags = a.take<unsigned>(4);
+    const size_t sb = std::max(spmm_scratch_bytes(z, std::max(wmax, rc), (int)sizeof(T)),
+                               spmm_scratch_bytes(z, 1, 8));
+    spmm_scr = a.take<char>(sb);
   }
 };
 
@@ -357,7 +361,7 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   if (s > 0) {
     {
       SVT_PROF("spmm_csc_recycled", spmm_bytes(z, n, m, s, sv), st);
-      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, st)));
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, W.spmm_scr, z, st, p->chunk_row_csc)));
     }
     SVT_TRY(block_sumsq<T>(W, n, s, W.Bt, W.ldb, &normB));
   }
@@ -375,12 +379,12 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     ++blocks;
     {
       SVT_PROF("spmm_csr", spmm_bytes(z, m, n, w, sv), st);
-      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, st)));
+      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, W.spmm_scr, z, st, p->chunk_row_csr)));
     }
     for (int it = 0; it < P.np; ++it) {
       SVT_PROF("spmm_power", spmm_bytes(z, n, m, w, sv) + spmm_bytes(z, m, n, w, sv), st);
-      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, W.X, W.ldw, w, W.Z, W.ldw, st)));
-      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Z, W.ldw, w, W.X, W.ldw, st)));
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, W.X, W.ldw, w, W.Z, W.ldw, W.spmm_scr, z, st, p->chunk_row_csc)));
+      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Z, W.ldw, w, W.X, W.ldw, W.spmm_scr, z, st, p->chunk_row_csr)));
     }
     double ssum = 0.0, scale = 0.0;
     SVT_TRY(block_sumsq<T>(W, m, w, W.X, W.ldw, &ssum, &scale));
@@ -422,7 +426,7 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     // B'^T = Y^T Q'
     {
       SVT_PROF("spmm_csc", spmm_bytes(z, n, m, w, sv), st);
-      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q + r, W.ldq, w, W.Bt + r, W.ldb, st)));
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q + r, W.ldq, w, W.Bt + r, W.ldb, W.spmm_scr, z, st, p->chunk_row_csc)));
     }
     double nb = 0.0;
     SVT_TRY(block_sumsq<T>(W, n, w, W.Bt + r, W.ldb, &nb));
@@ -440,8 +444,12 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
   }
   {
-    SVT_PROF("small_eig", 8.0 * 3 * r * r, st);
-    SVT_TRY(sym_eig(r, W.G, r, W.lam, W.Ub, r, W.eigw, kRefineSteps, st));
+    SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
+    SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2)));
+  }
+  {
+    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, kRefineSteps, st));
   }
   std::vector<double> lam(r);
   SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -452,6 +460,15 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   }
   SVT_CUDA(cudaStreamSynchronize(st));
   prof_flush();
+  if (g_prof_on) {  // sweep count of the binary32 Jacobi stage, kept as a pseudo-entry
+    int sweeps = 0;
+    if (cudaMemcpy(&sweeps, W.flags + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      const int id = prof_id("jacobi_sweeps");
+      g_prof[id].launches += 1;
+      g_prof[id].bytes += sweeps;
+    }
+  }
   for (int j = 0; j < r; ++j) {
     if (!std::isfinite(lam[j])) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
     o->sigma[j] = std::sqrt(std::max(lam[j], 0.0));
@@ -597,8 +614,10 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   SVT_LAUNCH_CHECK();
   for (int it = 0; it < P.power_steps; ++it) {
     SVT_PROF("init_power", spmm_bytes(nnz, m, n, 1, (int)sizeof(T)) + spmm_bytes(nnz, n, m, 1, (int)sizeof(T)), st);
-    SVT_TRY((launch_spmm_rows<T, double>(m, pat->row_ptr, pat->col_idx, a_csr, W.pv, 1, 1, W.pu, 1, st)));
-    SVT_TRY((launch_spmm_rows<T, double>(n, pat->col_ptr, pat->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1, st)));
+    SVT_TRY((launch_spmm_rows<T, double>(m, pat->row_ptr, pat->col_idx, a_csr, W.pv, 1, 1, W.pu, 1,
+                                         W.spmm_scr, nnz, st, pat->chunk_row_csr)));
+    SVT_TRY((launch_spmm_rows<T, double>(n, pat->col_ptr, pat->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1,
+                                         W.spmm_scr, nnz, st, pat->chunk_row_csc)));
     SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
     k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
     SVT_LAUNCH_CHECK();
@@ -787,42 +806,36 @@ extern "C" svt_status svt_spmm(const svt_pattern* p, int precision, int transpos
                                void* stream) {
   using namespace svt;
   if (!p || w < 0 || (p->nnz > 0 && !y_csr)) return fail(SVT_ERR_ARG, "spmm: bad arguments");
-  const int64_t rows_out = transpose ? p->n : p->m;
-  const int64_t rows_in = transpose ? p->m : p->n;
+  if (precision != SVT_FP64 && precision != SVT_MIXED_FP32) return fail(SVT_ERR_ARG, "spmm: unknown precision");
   if (w > 0 && (!W || !out || ldw < w || ldo < w)) return fail(SVT_ERR_ARG, "spmm: bad dense operands");
-  (void)rows_in;
+  if (w == 0) return SVT_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t z = p->nnz;
-  if (w == 0) return SVT_OK;
-  if (precision == SVT_FP64) {
-    const double* y = (const double*)y_csr;
-    DeviceBlock tmp;
+  const int64_t rows_out = transpose ? p->n : p->m;
+  const int elem = precision == SVT_FP64 ? 8 : 4;
+  DeviceBlock tmp;
+  Arena a;
+  a.take<char>(z * elem);
+  a.take<char>(spmm_scratch_bytes(z, w, elem));
+  SVT_TRY(tmp.alloc(a.off, s));
+  Arena b; b.base = (char*)tmp.ptr;
+  char* ycsc = b.take<char>(z * elem);
+  char* scr = b.take<char>(spmm_scratch_bytes(z, w, elem));
+  auto run = [&](auto tag) -> svt_status {
+    using T = decltype(tag);
+    const T* y = (const T*)y_csr;
     if (transpose) {
-      SVT_TRY(tmp.alloc(z * sizeof(double), s));
-      SVT_TRY(launch_gather<double>(z, p->perm, y, (double*)tmp.ptr, s));
-      SVT_TRY((launch_spmm_rows<double, double>(rows_out, p->col_ptr, p->row_idx, (double*)tmp.ptr,
-                                                 (const double*)W, ldw, w, (double*)out, ldo, s)));
+      SVT_TRY(launch_gather<T>(z, p->perm, y, (T*)ycsc, s));
+      SVT_TRY((launch_spmm_rows<T, T>(rows_out, p->col_ptr, p->row_idx, (const T*)ycsc, (const T*)W, ldw,
+                                       w, (T*)out, ldo, scr, z, s, p->chunk_row_csc)));
     } else {
-      SVT_TRY((launch_spmm_rows<double, double>(rows_out, p->row_ptr, p->col_idx, y,
-                                                 (const double*)W, ldw, w, (double*)out, ldo, s)));
+      SVT_TRY((launch_spmm_rows<T, T>(rows_out, p->row_ptr, p->col_idx, y, (const T*)W, ldw, w, (T*)out,
+                                       ldo, scr, z, s, p->chunk_row_csr)));
     }
-    SVT_CUDA(cudaStreamSynchronize(s));
-  } else if (precision == SVT_MIXED_FP32) {
-    const float* y = (const float*)y_csr;
-    DeviceBlock tmp;
-    if (transpose) {
-      SVT_TRY(tmp.alloc(z * sizeof(float), s));
-      SVT_TRY(launch_gather<float>(z, p->perm, y, (float*)tmp.ptr, s));
-      SVT_TRY((launch_spmm_rows<float, float>(rows_out, p->col_ptr, p->row_idx, (float*)tmp.ptr,
-                                               (const float*)W, ldw, w, (float*)out, ldo, s)));
-    } else {
-      SVT_TRY((launch_spmm_rows<float, float>(rows_out, p->row_ptr, p->col_idx, y, (const float*)W,
-                                               ldw, w, (float*)out, ldo, s)));
-    }
-    SVT_CUDA(cudaStreamSynchronize(s));
-  } else {
-    return fail(SVT_ERR_ARG, "spmm: unknown precision");
-  }
+    return SVT_OK;
+  };
+  SVT_TRY(precision == SVT_FP64 ? run(double(0)) : run(float(0)));
+  SVT_CUDA(cudaStreamSynchronize(s));
   return SVT_OK;
 }
 

@@ -21,33 +21,127 @@ constexpr int kRedBlocksPerSm = 8;
 
 int red_blocks() { return num_sms() * kRedBlocksPerSm; }
 
-template <typename T>
+template <typename T, int VEC>
+__device__ __forceinline__ void load_v(const T* p, T (&v)[VEC]) {
+  if constexpr (VEC == 1) {
+    v[0] = p[0];
+  } else if constexpr (VEC == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+}
+
+// Entries are split into chunks of C (warp w takes chunks w, w + #warps, ...).  Groups of
+// G lanes evaluate one entry each, UNR entries per group per step, so 32/G * UNR entries
+// (and their row gathers) are in flight per warp; all loads of a step are issued before
+// the dependent arithmetic.  Lane l of a group holds vectors l, l+G, ... (VEC elements
+// each) of U[p, :] for the current row p (read from the stored row of each entry,
+// reloaded when it changes) and multiplies them with the same slices of W[q, :]; a
+// shuffle tree over the group gives x_pq.  Loop trip counts are uniform across the warp
+// so every lane reaches the shuffles.
+template <typename T, int VEC, int G, int MAXV, int UNR>
 __global__ void __launch_bounds__(256)
-k_sampled_update(int64_t m, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                 const T* __restrict__ U, int64_t ldu, const T* __restrict__ W, int64_t ldw, int k,
-                 const T* __restrict__ a, T* __restrict__ y, T delta, double* __restrict__ part,
-                 unsigned* __restrict__ flags) {
+k_sampled_update(int64_t nnz, int64_t C, int64_t nchunks, const int32_t* __restrict__ csr_row,
+                 const int32_t* __restrict__ col_idx, const T* __restrict__ U, int64_t ldu,
+                 const T* __restrict__ W, int64_t ldw, int k, const T* __restrict__ a,
+                 T* __restrict__ y, T delta, double* __restrict__ part, unsigned* __restrict__ flags) {
   __shared__ double red[32];
+  constexpr int NG = 32 / G;
   const int lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane % G;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double s_d2 = 0.0, s_abs = 0.0, s_y2 = 0.0;
   bool bad = false;
-  for (int64_t p = wid; p < m; p += nw) {
-    const int beg = row_ptr[p], end = row_ptr[p + 1];
-    const T* up = U + p * ldu;
-    for (int e = beg + lane; e < end; e += 32) {
-      const T* wq = W + (int64_t)col_idx[e] * ldw;
-      T x = T(0);
-      for (int j = 0; j < k; ++j) x = fma(up[j], wq[j], x);
-      const T d = a[e] - x;
-      const T yn = fma(delta, d, y[e]);
-      y[e] = yn;
-      const double dd = (double)d, yy = (double)yn;
-      s_d2 = fma(dd, dd, s_d2);
-      s_abs += fabs(dd);
-      s_y2 = fma(yy, yy, s_y2);
-      bad |= !isfinite(yy);
+  for (int64_t chunk = wid; chunk < nchunks; chunk += nw) {
+    const int64_t beg = chunk * C;
+    const int64_t end = (beg + C < nnz) ? beg + C : nnz;
+    int64_t r = -1;
+    T u[MAXV][VEC];
+    for (int64_t base = beg; base < end; base += NG * UNR) {
+      // 1. independent loads of UNR entries per group
+      int64_t e[UNR];
+      bool v[UNR];
+      int32_t row[UNR], col[UNR];
+      T av[UNR], yv[UNR];
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        e[j] = base + j * NG + grp;
+        v[j] = e[j] < end;
+        row[j] = v[j] ? csr_row[e[j]] : 0;
+        col[j] = v[j] ? col_idx[e[j]] : 0;
+        av[j] = v[j] ? a[e[j]] : T(0);
+        yv[j] = v[j] ? y[e[j]] : T(0);
+      }
+      // 2. gathers of the W rows (independent of each other)
+      T wx[UNR][MAXV][VEC];
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        const T* wq = W + (int64_t)col[j] * ldw;
+#pragma unroll
+        for (int t = 0; t < MAXV; ++t) {
+          const int c0 = (gl + t * G) * VEC;
+          if (v[j] && c0 < k) load_v<T, VEC>(wq + c0, wx[j][t]);  // may read padding: masked below
+          else {
+#pragma unroll
+            for (int bb = 0; bb < VEC; ++bb) wx[j][t][bb] = T(0);
+          }
+        }
+      }
+      // 3. dot products with this lane's slices of U[row, :k] (reloaded on a new row)
+      T px[UNR];
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        px[j] = T(0);
+        if (v[j]) {
+          if (row[j] != r) {
+            r = row[j];
+            const T* up = U + r * ldu;
+#pragma unroll
+            for (int t = 0; t < MAXV; ++t) {
+              const int c0 = (gl + t * G) * VEC;
+              if (c0 < k) {
+                load_v<T, VEC>(up + c0, u[t]);
+#pragma unroll
+                for (int bb = 0; bb < VEC; ++bb)
+                  if (c0 + bb >= k) u[t][bb] = T(0);
+              } else {
+#pragma unroll
+                for (int bb = 0; bb < VEC; ++bb) u[t][bb] = T(0);
+              }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < MAXV; ++t) {
+            const int c0 = (gl + t * G) * VEC;
+#pragma unroll
+            for (int bb = 0; bb < VEC; ++bb)
+              if (c0 + bb < k) px[j] = fma(u[t][bb], wx[j][t][bb], px[j]);
+          }
+        }
+      }
+      // 4. group reductions (every lane takes part)
+#pragma unroll
+      for (int j = 0; j < UNR; ++j)
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) px[j] += __shfl_xor_sync(0xffffffffu, px[j], o);
+      // 5. residual and dual update
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        if (v[j] && gl == 0) {
+          const T d = av[j] - px[j];
+          const T yn = fma(delta, d, yv[j]);
+          y[e[j]] = yn;
+          const double dd = (double)d, yy = (double)yn;
+          s_d2 = fma(dd, dd, s_d2);
+          s_abs += fabs(dd);
+          s_y2 = fma(yy, yy, s_y2);
+          bad |= !isfinite(yy);
+        }
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NONFINITE);
@@ -77,15 +171,18 @@ __global__ void k_sumsq_part(int64_t count, const T* __restrict__ x, double* __r
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// out[c] = sum_b part[b * stride + c] for c < ncomp, in block order.
-__global__ void k_finish(int nblocks, int stride, int ncomp, const double* __restrict__ part,
-                         double* __restrict__ out) {
-  const int c = threadIdx.x;
-  if (c < ncomp) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * stride + c];
-    out[c] = s;
-  }
+// out[c] = sum_b part[b * stride + c] for c < ncomp (one block per component): thread t
+// adds blocks t, t + 256, ... in order, then a fixed shuffle tree combines the threads,
+// so the sum does not depend on scheduling.
+__global__ void __launch_bounds__(256)
+k_finish(int nblocks, int stride, int ncomp, const double* __restrict__ part,
+         double* __restrict__ out) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[(int64_t)b * stride + c];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0 && c < ncomp) out[c] = s;
 }
 
 template <typename T>
@@ -118,7 +215,7 @@ svt_status sumsq(int64_t count, const T* x, double* out, double* part, cudaStrea
   const int blocks = red_blocks();
   k_sumsq_part<T><<<blocks, 256, 0, s>>>(count, x, part, nullptr);
   SVT_LAUNCH_CHECK();
-  k_finish<<<1, 32, 0, s>>>(blocks, 1, 1, part, out);
+  k_finish<<<1, 256, 0, s>>>(blocks, 1, 1, part, out);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -140,15 +237,55 @@ svt_status gather_convert(int64_t count, const int32_t* src, const TS* vals, T* 
   return SVT_OK;
 }
 
+template <typename T, int VEC, int G, int MAXV>
+svt_status run_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W, int64_t ldw,
+                      int k, const T* a, T* y, double delta, double* part, unsigned* flags,
+                      cudaStream_t s) {
+  const int blocks = red_blocks();
+  const int64_t C = chunk_size(p->nnz > 0 ? p->nnz : 1);
+  const int64_t nchunks = ceil_div(p->nnz, C);
+  constexpr int UNR = (MAXV * VEC <= 16) ? 2 : 1;
+  k_sampled_update<T, VEC, G, MAXV, UNR><<<blocks, 256, 0, s>>>(p->nnz, C, nchunks, p->csr_row,
+                                                                p->col_idx, U, ldu, W, ldw, k, a, y,
+                                                                (T)delta, part, flags);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+template <typename T, int VEC>
+svt_status dispatch_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W, int64_t ldw,
+                           int k, const T* a, T* y, double delta, double* part, unsigned* flags,
+                           cudaStream_t s) {
+  const int nv = (int)ceil_div(k > 0 ? k : 1, VEC);
+  // at most 4 vectors per lane, as few lanes per entry as that allows
+#define SVT_RUN(G, MV) return run_update<T, VEC, G, MV>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)
+  if (nv <= 4) SVT_RUN(1, 4);
+  if (nv <= 8) SVT_RUN(2, 4);
+  if (nv <= 16) SVT_RUN(4, 4);
+  if (nv <= 32) SVT_RUN(8, 4);
+  if (nv <= 64) SVT_RUN(16, 4);
+  if (nv <= 128) SVT_RUN(32, 4);
+  if (nv <= 256) SVT_RUN(32, 8);
+  if (nv <= 512) SVT_RUN(32, 16);
+  SVT_RUN(32, 32);
+#undef SVT_RUN
+}
+
 template <typename T>
 svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W,
                           int64_t ldw, int k, const T* a, T* y, double delta, double* out3,
                           double* part, unsigned* flags, cudaStream_t s) {
-  const int blocks = red_blocks();
-  k_sampled_update<T><<<blocks, 256, 0, s>>>(p->m, p->row_ptr, p->col_idx, U, ldu, W, ldw, k, a,
-                                             y, (T)delta, part, flags);
-  SVT_LAUNCH_CHECK();
-  k_finish<<<1, 32, 0, s>>>(blocks, 3, 3, part, out3);
+  if (k > 1024) return fail(SVT_ERR_UNSUPPORTED, "sampled update: k = %d exceeds 1024", k);
+  constexpr int V = sizeof(T) == 4 ? 4 : 2;
+  const bool aligned = (reinterpret_cast<uintptr_t>(U) % 16 == 0) && (ldu % V == 0) &&
+                       (reinterpret_cast<uintptr_t>(W) % 16 == 0) && (ldw % V == 0);
+  if (p->nnz > 0) {
+    if (aligned) SVT_TRY((dispatch_update<T, V>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
+    else SVT_TRY((dispatch_update<T, 1>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
+  } else {
+    SVT_CUDA(cudaMemsetAsync(part, 0, 3 * red_blocks() * sizeof(double), s));
+  }
+  k_finish<<<3, 256, 0, s>>>(red_blocks(), 3, 3, part, out3);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
