@@ -38,6 +38,11 @@ the design notes; the CUDA path takes the same readings):
   unprojected column norm is discarded).
 * D_tau keeps sigma_j > tau (equality contributes zero either way); the returned
   factors are those of X^(i) = D_tau(Y^(i)).
+
+Parity unpinned: the cooling decisions of Algorithm 4 (when eps_thr is multiplied by
+beta) have no external pin -- no closed form or published trajectory exists -- so they
+are checked only for consistency with the rule and against the CUDA path.  Every other
+step is pinned by tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 
