@@ -143,6 +143,24 @@ svt_status svt_spmm(const svt_pattern* p, int precision, int transpose, const vo
                     const void* W, int64_t ldw, int32_t w, void* out, int64_t ldo,
                     void* stream);
 
+/* svt_spmm without any device allocation (the paper has no counterpart: this serves
+ * callers, not the method).  Same arguments, results and errors as svt_spmm, but its
+ * scratch memory comes from one fixed 32 MiB array inside this library instead of a fresh
+ * allocation, for callers that cannot allocate device memory when they need the product:
+ * a process whose other runtime has reserved nearly all GPU memory for its own pool, a
+ * latency-critical loop where an allocation or free would stall the device, or an
+ * application that only allows allocations at start-up.  A product whose scratch need
+ * (partial rows of its entry chunks, plus a column-order copy of Y when transpose = 1)
+ * exceeds the array returns SVT_ERR_UNSUPPORTED without queuing work.  Every GPU that
+ * loads the library keeps the array until the process exits.  All calls share it and
+ * its contents persist from call to call; nothing in it needs to start at zero, but
+ * calls that overlap on the GPU race on it.  The first call on a device looks up the
+ * array's address there and caches it; make that call before starting a stream
+ * capture. */
+svt_status svt_spmm_noalloc(const svt_pattern* p, int precision, int transpose,
+                            const void* y_csr, const void* W, int64_t ldw, int32_t w, void* out,
+                            int64_t ldo, void* stream);
+
 /* One sampled shrinkage-and-update pass (eq. (4)-(5) restricted to Lambda): for each
  * observed (p, q) in CSR order, x = sum_{j<k} U[p, j] * W[q, j], d = a - x,
  * y += delta * d.  U (m x k, ldu) and W (n x k, ldw) hold X^(i) = U W^T.  sums[0..2]

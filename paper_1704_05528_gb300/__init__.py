@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "sampled_update",
+__all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "spmm_noalloc", "sampled_update",
            "r4svd", "complete", "library", "launch_count", "profile_enable", "profile_reset", "profile_read",
            "FP64", "MIXED_FP32"]
 
@@ -153,6 +153,21 @@ def spmm(pattern: Pattern, y_csr, W, transpose=False, precision="fp64"):
     out = torch.empty((rows, w), device="cuda", dtype=dt)
     _check(library().svt_spmm(pattern.handle, prec, 1 if transpose else 0, _ptr(y), _ptr(W), max(w, 1),
                               w, _ptr(out), max(w, 1), _stream_ptr()))
+    return out
+
+
+def spmm_noalloc(pattern: Pattern, y_csr, W, out, transpose=False, precision="fp64"):
+    """Like spmm, but the library allocates nothing: its scratch is a fixed device array
+    (see svt_spmm_noalloc in the C header).  The caller supplies `out` (rows x w)."""
+    prec = _prec(precision)
+    dt = _vdtype(prec)
+    assert y_csr.is_cuda and y_csr.dtype == dt and y_csr.is_contiguous()
+    assert W.is_cuda and W.dtype == dt and W.is_contiguous() and W.dim() == 2
+    w = W.shape[1]
+    rows = pattern.n if transpose else pattern.m
+    assert out.is_cuda and out.dtype == dt and out.is_contiguous() and tuple(out.shape) == (rows, w)
+    _check(library().svt_spmm_noalloc(pattern.handle, prec, 1 if transpose else 0, _ptr(y_csr), _ptr(W),
+                                      max(w, 1), w, _ptr(out), max(w, 1), _stream_ptr()))
     return out
 
 

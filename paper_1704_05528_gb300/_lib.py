@@ -53,6 +53,7 @@ SIGNATURES = {
     "svt_pattern_export": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "svt_gaussian_block": (C.c_int, [_U64, _U32, _U32, _I64, _I32, _P, _I64, _P]),
     "svt_spmm": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _I64, _I32, _P, _I64, _P]),
+    "svt_spmm_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _I64, _I32, _P, _I64, _P]),
     "svt_sampled_update": (C.c_int, [_P, C.c_int, _P, _I64, _P, _I64, _I32, _P, _P, _D, _PD, _P]),
     "svt_r4svd": (C.c_int, [_P, _P, _P, _I64, _I32, _D, _U32, C.POINTER(Options), _P, _I64, _P,
                             _P, _I64, _PI32, _PD, _PI32]),
