@@ -19,3 +19,9 @@ from .fastsvt import (  # noqa: F401
     SVTResult,
     R4SVDResult,
 )
+from .adjoint import (  # noqa: F401
+    d_tau_jvp_dense,
+    d_tau_dtau_dense,
+    svt_unrolled_grad,
+    UnrolledResult,
+)

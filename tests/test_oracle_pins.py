@@ -392,3 +392,61 @@ def test_planted_missing_shift_breaks_d_tau():
     wrong = (Uy[:, keep] * sy[keep]) @ Vty[keep]
     want = (U * np.maximum(s - 2.5, 0)) @ V.T
     assert not np.allclose(wrong, want, atol=1e-6)
+
+
+# ------------------------------------------------- derivatives of unrolled SVT
+@pytest.mark.parametrize("m,n", [(9, 7), (6, 8), (10, 10)])
+def test_d_tau_jvp_matches_finite_differences(m, n):
+    """The full-SVD derivative of D_tau against central differences of eq. (5)."""
+    rng = np.random.default_rng(m * 10 + n)
+    Y = 3.0 * rng.standard_normal((m, n))
+    Z, Z2 = rng.standard_normal((m, n)), rng.standard_normal((m, n))
+    tau, h = 2.0, 1e-6
+    fd = (oracle.d_tau_dense(Y + h * Z, tau) - oracle.d_tau_dense(Y - h * Z, tau)) / (2 * h)
+    J = oracle.d_tau_jvp_dense(Y, tau, Z)
+    assert np.linalg.norm(J - fd) < 1e-7 * np.linalg.norm(fd)
+    # D_tau is a proximal map, so its Jacobian is symmetric
+    assert abs(np.sum(J * Z2) - np.sum(Z * oracle.d_tau_jvp_dense(Y, tau, Z2))) < 1e-12
+    fdt = (oracle.d_tau_dense(Y, tau + h) - oracle.d_tau_dense(Y, tau - h)) / (2 * h)
+    assert np.linalg.norm(oracle.d_tau_dtau_dense(Y, tau) - fdt) < 1e-7
+
+
+def test_d_tau_jvp_kept_block_closed_form():
+    """On the kept/kept block: (1 - tau/(s_i+s_j)) Zhat_ij + tau/(s_i+s_j) Zhat_ji."""
+    rng = np.random.default_rng(3)
+    U = _householder_orthogonal(rng, 6)
+    V = _householder_orthogonal(rng, 6)
+    s = np.array([9.0, 7.0, 5.0, 3.0, 2.0, 1.0])
+    Y = (U * s) @ V.T
+    Z = rng.standard_normal((6, 6))
+    tau = 4.0
+    dF = U.T @ oracle.d_tau_jvp_dense(Y, tau, Z) @ V
+    Zh = U.T @ Z @ V
+    for i in range(3):
+        for j in range(3):
+            c = tau / (s[i] + s[j])
+            want = Zh[i, i] if i == j else (1 - c) * Zh[i, j] + c * Zh[j, i]
+            assert abs(dF[i, j] - want) < 1e-12
+    assert np.allclose(dF[3:, 3:], 0.0, atol=1e-12)  # complement/complement block vanishes
+
+
+def test_unrolled_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    m, n = 30, 25
+    M = rng.standard_normal((m, 2)) @ rng.standard_normal((2, n))
+    flat = rng.choice(m * n, size=300, replace=False)
+    rows, cols, vals = flat // n, flat % n, M[flat // n, flat % n]
+    hflat = rng.choice(np.setdiff1d(np.arange(m * n), flat), size=50, replace=False)
+    hr, hc = hflat // n, hflat % n
+    tau, delta, T = 20.0, 1.5, 6
+    r = oracle.svt_unrolled_grad(m, n, rows, cols, vals, hr, hc, M[hr, hc], tau, delta, T)
+
+    def f(v=vals, t=tau, d=delta):
+        return oracle.svt_unrolled_grad(m, n, rows, cols, v, hr, hc, M[hr, hc], t, d, T, k0=r.k0,
+                                        with_grad=False).loss
+    h = 1e-5
+    assert abs(r.grad_tau - (f(t=tau + h) - f(t=tau - h)) / (2 * h)) < 1e-7 * max(1, abs(r.grad_tau))
+    assert abs(r.grad_delta - (f(d=delta + h) - f(d=delta - h)) / (2 * h)) < 1e-7 * max(1, abs(r.grad_delta))
+    direction = rng.standard_normal(vals.shape)
+    fd = (f(v=vals + h * direction) - f(v=vals - h * direction)) / (2 * h)
+    assert abs(np.dot(r.grad_vals, direction) - fd) < 1e-7 * max(1, abs(fd))
