@@ -203,6 +203,78 @@ svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                         double* S, double* V, int32_t cap, svt_result* res,
                         svt_iter_log* log, int32_t log_cap);
 
+/* ------------------------------------------------------------------ unrolled SVT */
+typedef struct svt_unrolled_params {
+  int32_t steps;             /* unrolled iterations T >= 1                                   */
+  int32_t checkpoint_every;  /* forward state kept every this many iterations (default 5)   */
+  int32_t cg_maxit;          /* step cap of each batched CG solve (default 1000)             */
+  int32_t ritz_maxit;        /* cap on refinement steps per iteration (default 100); 0 turns
+                                the refinement off and differentiates plain R4SVD output     */
+  double cg_tol;             /* relative residual at which a CG column stops (default 1e-10
+                                for SVT_FP64, 1e-6 for SVT_MIXED_FP32)                       */
+  double ritz_tol;           /* refinement stops once ||Y v_i - s_i u_i|| <= ritz_tol * s_1
+                                for every kept triplet (default 1e-11 for SVT_FP64, 2e-6 for
+                                SVT_MIXED_FP32); the first dropped one needs only to be
+                                placed below tau                                             */
+} svt_unrolled_params;
+
+typedef struct svt_unrolled_info {
+  int32_t k0;            /* kick-start multiple of the initialisation (held fixed)        */
+  int32_t k_final;       /* rank of X^(T)                                                 */
+  int32_t r_final;       /* revealed rank of the last R4SVD                              */
+  int32_t cg_iters;      /* conjugate-gradient steps over all adjoint solves             */
+  int32_t cg_capped;     /* adjoint solves that stopped at cg_maxit before cg_tol        */
+  int32_t ritz_steps;    /* refinement steps over the forward pass                       */
+  int32_t ritz_capped;   /* forward iterations whose refinement stopped short of ritz_tol
+                            (step cap, or residuals stalled at the rounding floor)        */
+  int32_t ritz_grown;    /* blocks appended to certify a kept set (no dropped Ritz value) */
+  double loss;
+  double seconds_forward;
+  double seconds_total;
+} svt_unrolled_info;
+
+/* Defaults above for the given precision (SVT_FP64 or SVT_MIXED_FP32); steps = 20. */
+void svt_unrolled_default_params(svt_unrolled_params* p, int precision);
+
+/* Unrolled SVT and its gradient (the paper differentiates nothing; this builds on its
+ * iteration, eq. (4), with D_tau of eq. (5) evaluated by R4SVD, Algorithm 3).  Runs
+ * T = p->steps iterations Y^(1) = k0 delta P_Lambda(A), X^(i) = D_tau(Y^(i)),
+ * Y^(i+1) = Y^(i) + delta P_Lambda(A - X^(i)) with no stop test (k0 as in svt_complete,
+ * then held fixed), evaluates L = mean over the nheld held-out entries of
+ * (X^(T) - A)^2, and returns dL/dvals (grad_vals[nnz], caller order),
+ * out3 = {L, dL/dtau, dL/ddelta} and X^(T) on the held-out entries (x_held[nheld]).
+ *
+ * Forward.  Each R4SVD result is refined by power steps Q <- orth(Y Y^T Q) on its whole
+ * basis (the power scheme of Algorithms 1-3), each followed by a Rayleigh-Ritz step,
+ * until the kept triplets meet the residual bound ritz_tol and the first dropped one is
+ * placed below tau (or the residuals stop falling: the rounding floor);
+ * D_tau is then that of Y to this bound and the gradient is that of exact unrolled SVT.
+ * While every Ritz value exceeds tau the basis grows by Gaussian blocks of opt->dt
+ * columns, as in R4SVD; at the rank cap the kept set cannot be certified and the call
+ * fails with SVT_ERR_UNSUPPORTED (raise opt->r_max).  The refined basis is what the next
+ * iteration recycles.
+ *
+ * Reverse.  The forward state (Y, the recycled basis, the cooled threshold) is kept every
+ * checkpoint_every iterations and each segment is replayed from it.  The adjoint of D_tau
+ * (its Jacobian is symmetric) is a closed form on the kept block and, for the coupling
+ * with the rest of the spectrum, shifted systems (s_i^2 - Y_perp^T Y_perp) w_i = b_i
+ * solved by batched conjugate gradients with sparse products of Y only.
+ *
+ * Index and value arrays may be host or device memory (values double for SVT_FP64, float
+ * for SVT_MIXED_FP32); outputs are binary64, host or device.  grad_vals NULL skips the
+ * reverse pass (out3 = {L, NaN, NaN}).  p NULL means the defaults;
+ * info (host) may be NULL.  Errors: SVT_ERR_ARG (sizes, tau/delta <= 0, bad parameters),
+ * the pattern errors of svt_pattern_create for either index set, SVT_ERR_NUMERIC
+ * (non-finite iterate or CG residual, basis breakdown), SVT_ERR_UNSUPPORTED (see above
+ * and svt_complete's rank cap), SVT_ERR_CUDA. */
+svt_status svt_unrolled_grad(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                             const int32_t* cols, const void* vals, int64_t nheld,
+                             const int32_t* held_rows, const int32_t* held_cols,
+                             const void* held_vals, double tau, double delta,
+                             const svt_unrolled_params* p, const svt_options* opt,
+                             double* grad_vals, double* x_held, double* out3,
+                             svt_unrolled_info* info);
+
 /* ------------------------------------------------------------------ profiling */
 /* Per-kernel-class timing (no counterpart in the paper; the analogue of its
  * per-iteration timing figures).  When enabled, the solver brackets each kernel class

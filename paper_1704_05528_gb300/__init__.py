@@ -16,7 +16,7 @@ from . import _lib as L
 
 __all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "spmm_noalloc", "sampled_update",
            "r4svd", "complete", "library", "launch_count", "profile_enable", "profile_reset", "profile_read",
-           "FP64", "MIXED_FP32"]
+           "unrolled_grad", "unrolled_params", "SVTUnrolled", "FP64", "MIXED_FP32"]
 
 FP64 = L.SVT_FP64
 MIXED_FP32 = L.SVT_MIXED_FP32
@@ -320,3 +320,92 @@ def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", l
                       rel_residual=res.rel_residual, mae=res.mae, k0=res.k0, spec_norm=res.spec_norm,
                       r=res.r, seconds_pattern=res.seconds_pattern, seconds_total=res.seconds_total,
                       log=_log_list(logbuf, res.log_len))
+
+
+def unrolled_params(precision="fp64", **kw):
+    """svt_unrolled_params with the library defaults for `precision`, then `kw` applied."""
+    up = L.UnrolledParams()
+    library().svt_unrolled_default_params(C.byref(up), _prec(precision))
+    names = {f[0] for f in L.UnrolledParams._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown unrolled parameter {k!r}")
+        setattr(up, k, v)
+    return up
+
+
+_UNROLLED_KEYS = ("checkpoint_every", "cg_maxit", "ritz_maxit", "cg_tol", "ritz_tol")
+
+
+def unrolled_grad(m, n, rows, cols, vals, held_rows, held_cols, held_vals, tau, delta, steps,
+                  precision="fp64", with_grad=True, **kw):
+    """Unrolled SVT and its gradient (svt_unrolled_grad): returns a dict with the held-out
+    MSE `loss`, `grad_vals` (numpy, input order), `grad_tau`, `grad_delta`, `x_held` and
+    the solver info.  Index and value arrays are host (numpy) arrays.  Keywords named like
+    the fields of svt_unrolled_params (checkpoint_every, cg_tol, cg_maxit, ritz_tol,
+    ritz_maxit) set those; the rest go to the solver options.  with_grad=False runs the
+    forward only (grad_vals None, grad_tau and grad_delta NaN)."""
+    _torch()
+    up = unrolled_params(precision, steps=int(steps),
+                         **{k: kw.pop(k) for k in list(kw) if k in _UNROLLED_KEYS})
+    o = options(precision, **kw)
+    o.stream = _stream_ptr().value
+    np_dt = np.float64 if o.precision == FP64 else np.float32
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    v = np.ascontiguousarray(vals, dtype=np_dt)
+    hr = np.ascontiguousarray(held_rows, dtype=np.int32)
+    hc = np.ascontiguousarray(held_cols, dtype=np.int32)
+    hv = np.ascontiguousarray(held_vals, dtype=np_dt)
+    grad = np.zeros(r.shape[0])
+    xh = np.zeros(hr.shape[0])
+    out3 = np.zeros(3)
+    info = L.UnrolledInfo()
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check(library().svt_unrolled_grad(m, n, r.shape[0], p(r), p(c), p(v), hr.shape[0], p(hr), p(hc),
+                                       p(hv), float(tau), float(delta), C.byref(up), C.byref(o),
+                                       p(grad) if with_grad else None, p(xh), p(out3), C.byref(info)))
+    keys = [f[0] for f in L.UnrolledInfo._fields_]
+    return dict(loss=float(out3[0]), grad_vals=grad if with_grad else None, grad_tau=float(out3[1]),
+                grad_delta=float(out3[2]),
+                x_held=xh, info={k: getattr(info, k) for k in keys})
+
+
+def _make_unrolled_function():
+    torch = _torch()
+
+    class SVTUnrolled(torch.autograd.Function):
+        """Held-out MSE of unrolled SVT as a differentiable function of the observed
+        values, tau and delta; backward returns the gradients from the hand-written
+        adjoint (svt_unrolled_grad), scaled by the incoming gradient."""
+
+        @staticmethod
+        def forward(ctx, vals, tau, delta, problem):
+            res = unrolled_grad(problem["m"], problem["n"], problem["rows"], problem["cols"],
+                                vals.detach().cpu().numpy(), problem["held_rows"], problem["held_cols"],
+                                problem["held_vals"], float(tau), float(delta), problem["steps"],
+                                **problem.get("options", {}))
+            ctx.save_for_backward(torch.from_numpy(res["grad_vals"]).to(vals.dtype),
+                                  torch.tensor(res["grad_tau"], dtype=torch.float64),
+                                  torch.tensor(res["grad_delta"], dtype=torch.float64))
+            ctx.info = res["info"]
+            return torch.tensor(res["loss"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            gv, gt, gd = ctx.saved_tensors
+            return g * gv, (g * gt).to(torch.float64), (g * gd).to(torch.float64), None
+
+    return SVTUnrolled
+
+
+class _LazyUnrolled:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyUnrolled._fn is None:
+            _LazyUnrolled._fn = _make_unrolled_function()
+        return _LazyUnrolled._fn.apply(*args)
+
+
+SVTUnrolled = _LazyUnrolled()

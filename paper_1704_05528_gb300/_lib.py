@@ -37,6 +37,18 @@ class Result(C.Structure):
                 ("seconds_pattern", C.c_double), ("seconds_total", C.c_double)]
 
 
+class UnrolledParams(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("checkpoint_every", C.c_int32), ("cg_maxit", C.c_int32),
+                ("ritz_maxit", C.c_int32), ("cg_tol", C.c_double), ("ritz_tol", C.c_double)]
+
+
+class UnrolledInfo(C.Structure):
+    _fields_ = [("k0", C.c_int32), ("k_final", C.c_int32), ("r_final", C.c_int32),
+                ("cg_iters", C.c_int32), ("cg_capped", C.c_int32), ("ritz_steps", C.c_int32),
+                ("ritz_capped", C.c_int32), ("ritz_grown", C.c_int32),
+                ("loss", C.c_double), ("seconds_forward", C.c_double), ("seconds_total", C.c_double)]
+
+
 _P = C.c_void_p
 _I32, _I64, _U32, _U64, _D = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
 _PI32 = C.POINTER(C.c_int32)
@@ -61,6 +73,10 @@ SIGNATURES = {
     "svt_profile_reset": (None, []),
     "svt_launch_count": (C.c_int64, []),
     "svt_profile_read": (C.c_int, [C.c_int, _P, C.POINTER(C.c_int64), _PD, _PD]),
+    "svt_unrolled_default_params": (None, [C.POINTER(UnrolledParams), C.c_int]),
+    "svt_unrolled_grad": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P, _D, _D,
+                                     C.POINTER(UnrolledParams), C.POINTER(Options), _P, _P, _P,
+                                     C.POINTER(UnrolledInfo)]),
     "svt_complete": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _D, _D, _D, _I32,
                                C.POINTER(Options), _P, _P, _P, _I32, C.POINTER(Result),
                                C.POINTER(IterLog), _I32]),

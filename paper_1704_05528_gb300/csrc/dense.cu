@@ -103,6 +103,35 @@ __global__ void k_reduce_parts(int p, int q, int splits, const double* __restric
   }
 }
 
+// The same sums when there are many splits and few outputs: one warp per output, lane l
+// adding splits l, l + 32, ... in order, then a fixed shuffle tree.
+__global__ void k_reduce_parts_warp(int p, int q, int splits, const double* __restrict__ part,
+                                    double* __restrict__ C, int64_t ldc, int symmetric) {
+  const int64_t pq = (int64_t)p * q;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < pq; t += nw) {
+    const int64_t a = t / q, b = t % q;
+    const int64_t src = (symmetric && (a / TN_TILE) > (b / TN_TILE)) ? b * q + a : t;
+    double s = 0.0;
+    for (int z = lane; z < splits; z += 32) s += part[(int64_t)z * pq + src];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) C[a * ldc + b] = s;
+  }
+}
+
+int grid_cap(int64_t work, int threads, int per_sm);
+
+void launch_reduce_parts(int p, int q, int splits, const double* part, double* C, int64_t ldc,
+                         int symmetric, cudaStream_t s) {
+  const int64_t pq = (int64_t)p * q;
+  if (splits > 32 && pq <= 65536)
+    k_reduce_parts_warp<<<grid_cap(pq * 32, 256, 8), 256, 0, s>>>(p, q, splits, part, C, ldc, symmetric);
+  else
+    k_reduce_parts<<<grid_cap(pq, 256, 8), 256, 0, s>>>(p, q, splits, part, C, ldc, symmetric);
+}
+
 int tn_splits(int64_t M, int p, int q) {
   const int64_t tiles = ceil_div(p, TN_TILE) * ceil_div(q, TN_TILE);
   int64_t want = ceil_div((int64_t)num_sms() * 4, tiles);
@@ -163,6 +192,64 @@ k_gemm_nn(int64_t M, int p, int q, double alpha, const TA* __restrict__ A, int64
       double v = alpha * (double)acc[a][b];
       if (beta != 0.0) v += beta * (double)Cin[i * ldcin + j];
       C[i * ldc + j] = (TC)v;
+    }
+  }
+}
+
+// The binary32 case of k_gemm_nn: C = alpha A B + beta Cin with a 128 x 64 output tile per
+// block and 8 x 4 outputs per thread (A staged k-major so each thread reads its 8 rows and
+// 4 columns as float4), epilogue in binary32 (binary64 runs at a small fraction of the
+// binary32 rate on this GPU).
+__global__ void __launch_bounds__(256)
+k_gemm_nn_f32(int64_t M, int p, int q, float alpha, const float* __restrict__ A, int64_t lda,
+              const double* __restrict__ B, int64_t ldb, float beta, const float* Cin,
+              int64_t ldcin, float* C, int64_t ldc) {
+  __shared__ __align__(16) float As[32][132];  // As[k][row]
+  __shared__ __align__(16) float Bs[32][64];   // Bs[k][col]
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * 128;
+  const int j0 = blockIdx.x * 64;
+  float acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < p; k0 += 32) {
+    for (int t = threadIdx.x; t < 128 * 32; t += 256) {
+      const int rr = t >> 5, cc = t & 31;
+      const int64_t i = i0 + rr;
+      As[cc][rr] = (i < M && k0 + cc < p) ? A[i * lda + k0 + cc] : 0.f;
+    }
+    for (int t = threadIdx.x; t < 32 * 64; t += 256) {
+      const int rr = t >> 6, cc = t & 63;
+      Bs[rr][cc] = (k0 + rr < p && j0 + cc < q) ? (float)B[(int64_t)(k0 + rr) * ldb + j0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+      const float4 bq = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int64_t i = i0 + ty * 8 + a;
+    if (i >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + tx * 4 + b;
+      if (j >= q) continue;
+      float v = alpha * acc[a][b];
+      if (beta != 0.f) v = fmaf(beta, Cin[i * ldcin + j], v);
+      C[i * ldc + j] = v;
     }
   }
 }
@@ -280,7 +367,7 @@ svt_status gemm_tn(int64_t M, int p, int q, const TA* A, int64_t lda, const TB* 
   const int sym = (A == (const TA*)(const void*)B && p == q && lda == ldb) ? 1 : 0;
   k_gemm_tn_part<TA, TB><<<grid, 256, 0, s>>>(M, p, q, A, lda, B, ldb, rows, part, sym);
   SVT_LAUNCH_CHECK();
-  k_reduce_parts<<<grid_cap((int64_t)p * q, 256, 8), 256, 0, s>>>(p, q, used, part, C, ldc, sym);
+  launch_reduce_parts(p, q, used, part, C, ldc, sym, s);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -301,9 +388,15 @@ svt_status gemm_nn(int64_t M, int p, int q, double alpha, const TA* A, int64_t l
     }
     return SVT_OK;
   }
-  using TACC = typename std::conditional<sizeof(TA) == 8 || sizeof(TC) == 8, double, float>::type;
-  k_gemm_nn<TA, TC, TACC><<<grid, 256, 0, s>>>(M, p, q, alpha, A, lda, B, ldb, beta, Cin, ldcin,
-                                               C, ldc);
+  if constexpr (sizeof(TA) == 4 && sizeof(TC) == 4) {
+    const dim3 g32((unsigned)ceil_div(q, 64), (unsigned)ceil_div(M, 128));
+    k_gemm_nn_f32<<<g32, 256, 0, s>>>(M, p, q, (float)alpha, A, lda, B, ldb, (float)beta, Cin, ldcin,
+                                      C, ldc);
+  } else {
+    using TACC = typename std::conditional<sizeof(TA) == 8 || sizeof(TC) == 8, double, float>::type;
+    k_gemm_nn<TA, TC, TACC><<<grid, 256, 0, s>>>(M, p, q, alpha, A, lda, B, ldb, beta, Cin, ldcin,
+                                                 C, ldc);
+  }
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -321,7 +414,7 @@ svt_status colsumsq(int64_t M, int w, const T* X, int64_t ldx, double* sums, dou
   const int blocks = (int)ceil_div(M > 0 ? M : 1, rows);
   k_colsumsq_part<T><<<blocks, 256, 0, s>>>(M, w, X, ldx, rows, part);
   SVT_LAUNCH_CHECK();
-  k_reduce_parts<<<grid_cap(w, 256, 8), 256, 0, s>>>(1, w, blocks, part, sums, w, 0);
+  launch_reduce_parts(1, w, blocks, part, sums, w, 0, s);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }

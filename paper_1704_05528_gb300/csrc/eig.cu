@@ -39,20 +39,33 @@ __device__ __forceinline__ void rr_pair(int step, int i, int N, int* p, int* q) 
   }
 }
 
+// Rotate the pair (p, q) while its coupling is significant against the gap of its
+// diagonal entries (what limits the eigenvector accuracy) and above binary32 rounding
+// noise of the entries themselves; the binary64 refinement resolves the rest.
+__device__ __forceinline__ bool jac_active(float app, float aqq, float apq, float scale) {
+  const float mag = fabsf(apq);
+  return mag > 1e-6f * fabsf(app - aqq) && mag > 4e-7f * (fabsf(app) + fabsf(aqq)) &&
+         mag > 1e-30f * scale;
+}
+
 // A: r x r working copy (row-major), V: r x r eigenvector estimate (columns).
 // Each step of a sweep rotates the N/2 disjoint planes of the round-robin pairing at once.
 // Because the planes are disjoint, the two-sided update A <- J^T A J and V <- V J splits
 // into independent 2x2 blocks (rows of pair i, columns of pair j): thread (i, j) reads
 // its block, applies J_i^T . J_j (V only . J_j) and writes it back, so a step needs two
-// barriers.  With N = r rounded up to even, a pair whose partner is the padding index r
-// rotates nothing and has a single row / column.
+// barriers; a step in which no pair rotates skips the update and its barrier.  After a
+// sweep that rotated, one pass over all pairs decides whether another sweep would rotate
+// anything (the matrix is unchanged by a sweep without rotations, so this is the same
+// test as running that sweep).  With N = r rounded up to even, a pair whose partner is
+// the padding index r rotates nothing and has a single row / column.
 __global__ void __launch_bounds__(kJacThreads)
 k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* gV,
            int max_sweeps, int use_smem, int* sweeps_out) {
   extern __shared__ float dyn[];
   __shared__ float cs_c[kJacThreads / 2 + 1], cs_s[kJacThreads / 2 + 1];
   __shared__ int pp[kJacThreads / 2 + 1], qq[kJacThreads / 2 + 1];
-  __shared__ int active_any;
+  __shared__ int active_any, check_any;
+  __shared__ int step_flag[3];
   __shared__ float scale;
   float* A = use_smem ? dyn : gA;
   float* V = use_smem ? dyn + r * r : gV;
@@ -69,19 +82,19 @@ k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* g
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) scale = mx;
   }
+  if (tid < 3) step_flag[tid] = 0;
   __syncthreads();
   const int N = (r + 1) & ~1;
   const int npairs = N / 2;
   // 2D layout of the block updates: ty = tid / 32 walks pairs i, tx = tid % 32 pairs j
   const int ty = tid >> 5, tx = tid & 31;
   int sweep = 0;
+  int gstep = 0;  // steps over all sweeps: step_flag[gstep % 3] marks a rotating step
+  if (tid == 0) active_any = 0;
+  __syncthreads();
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) active_any = 0;
-    __syncthreads();
-    for (int step = 0; step < N - 1; ++step) {
-      // Rotate a pair while its coupling is significant against the gap of its diagonal
-      // entries (what limits the eigenvector accuracy) and above binary32 rounding noise
-      // of the entries themselves; the binary64 refinement resolves the rest.
+    for (int step = 0; step < N - 1; ++step, ++gstep) {
+      int* flag = &step_flag[gstep % 3];
       for (int i = tid; i < npairs; i += blockDim.x) {
         int p, q;
         rr_pair(step, i, N, &p, &q);
@@ -90,21 +103,24 @@ k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* g
         if (q < r) {
           const float apq = A[p * r + q];
           const float app = A[p * r + p], aqq = A[q * r + q];
-          const float mag = fabsf(apq);
-          if (mag > 1e-6f * fabsf(app - aqq) && mag > 4e-7f * (fabsf(app) + fabsf(aqq)) &&
-              mag > 1e-30f * scale) {
+          if (jac_active(app, aqq, apq, scale)) {
             const float theta = (aqq - app) / (2.f * apq);
             float t;
             if (fabsf(theta) > 1e15f) t = 0.5f / theta;
             else t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
             c = rsqrtf(1.f + t * t);
             sn = t * c;
-            active_any = 1;
+            *flag = 1;
           }
         }
         cs_c[i] = c; cs_s[i] = sn; pp[i] = p; qq[i] = q;
       }
       __syncthreads();
+      // The slot two steps ahead is free: its writers have not passed this barrier's
+      // successor yet.  Every thread reads the same *flag (no writer until step gstep + 3).
+      if (tid == 0) step_flag[(gstep + 2) % 3] = 0;
+      if (!*flag) continue;
+      if (tid == 0) active_any = 1;
       for (int i = ty; i < npairs; i += kJacThreads / 32) {
         const int pi = pp[i], qi = qq[i];
         const float ci = cs_c[i], si = cs_s[i];
@@ -141,7 +157,21 @@ k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* g
       }
       __syncthreads();
     }
-    if (!active_any) break;
+    __syncthreads();
+    if (!active_any) break;  // nothing rotated in this sweep
+    // would another sweep rotate anything?
+    if (tid == 0) check_any = 0;
+    __syncthreads();
+    for (int t = tid; t < r * r; t += blockDim.x) {
+      const int a = t / r, b = t - (t / r) * r;
+      if (a < b && jac_active(A[a * r + a], A[b * r + b], A[a * r + b], scale)) check_any = 1;
+    }
+    __syncthreads();
+    if (!check_any) {
+      ++sweep;
+      break;
+    }
+    if (tid == 0) active_any = 0;
     __syncthreads();
   }
   if (use_smem) {
@@ -151,21 +181,25 @@ k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* g
 }
 
 // C = op(A) B + beta Cin for r x r row-major binary64 matrices (op(A) = A or A^T), one
-// 16 x 16 output tile per block.
+// 8 x 8 output tile per block: binary64 runs at a small fraction of the binary32 rate, so
+// small tiles spread an r = 100 product over all SMs instead of a third of them.
+constexpr int kSgTile = 8;
+
 template <bool TRANS_A>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSgTile * kSgTile)
 k_small_gemm(int r, const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
              double beta, const double* __restrict__ Cin, double* __restrict__ C) {
-  __shared__ double As[16][17];
-  __shared__ double Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+  constexpr int T = kSgTile;
+  __shared__ double As[T][T + 1];
+  __shared__ double Bs[T][T + 1];
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  const int i = blockIdx.y * T + ty, j = blockIdx.x * T + tx;
   double acc = 0.0;
-  for (int k0 = 0; k0 < r; k0 += 16) {
+  for (int k0 = 0; k0 < r; k0 += T) {
     const int ka = k0 + tx, kb = k0 + ty;
     if (TRANS_A) {
-      // op(A)[i][k] = A[k][i]: load rows k0.. of A, columns blockIdx.y*16 ..
-      const int ia = blockIdx.y * 16 + tx, kk = k0 + ty;
+      // op(A)[i][k] = A[k][i]: load rows k0.. of A, columns blockIdx.y*T ..
+      const int ia = blockIdx.y * T + tx, kk = k0 + ty;
       As[tx][ty] = (ia < r && kk < r) ? A[(int64_t)kk * lda + ia] : 0.0;
     } else {
       As[ty][tx] = (i < r && ka < r) ? A[(int64_t)i * lda + ka] : 0.0;
@@ -173,7 +207,7 @@ k_small_gemm(int r, const double* __restrict__ A, int64_t lda, const double* __r
     Bs[ty][tx] = (kb < r && j < r) ? B[(int64_t)kb * r + j] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+    for (int kk = 0; kk < T; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
     __syncthreads();
   }
   if (i < r && j < r) {
@@ -300,11 +334,11 @@ svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* 
   double* lamw = E + rr;
   double* part = lamw + r + 8;
   (void)part;
-  const dim3 grid((unsigned)ceil_div(r, 16), (unsigned)ceil_div(r, 16));
+  const dim3 grid((unsigned)ceil_div(r, kSgTile), (unsigned)ceil_div(r, kSgTile));
   auto gemm = [&](bool ta, const double* A_, int64_t lda_, const double* B_, double beta,
                   const double* Cin_, double* C_) -> svt_status {
-    if (ta) k_small_gemm<true><<<grid, 256, 0, s>>>(r, A_, lda_, B_, beta, Cin_, C_);
-    else k_small_gemm<false><<<grid, 256, 0, s>>>(r, A_, lda_, B_, beta, Cin_, C_);
+    if (ta) k_small_gemm<true><<<grid, kSgTile * kSgTile, 0, s>>>(r, A_, lda_, B_, beta, Cin_, C_);
+    else k_small_gemm<false><<<grid, kSgTile * kSgTile, 0, s>>>(r, A_, lda_, B_, beta, Cin_, C_);
     SVT_LAUNCH_CHECK();
     return SVT_OK;
   };

@@ -1,0 +1,440 @@
+// Shared pieces of the SVT driver: parameters, device work buffers, the R4SVD routine
+// (Algorithm 3; Algorithm 2 when nothing is recycled) and the per-kernel-class profiler.
+// Included by the fast-SVT driver and by the unrolled / adjoint driver.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace svt {
+
+
+using clk = std::chrono::steady_clock;
+inline double seconds_since(clk::time_point t0) {
+  return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+// ------------------------------------------------------------------ profiler
+// When enabled, each kernel class launched by the driver is bracketed by CUDA events
+// on the launching stream; elapsed times are folded in at the driver's sync points,
+// together with the algorithmic bytes that the class must move.
+struct ProfEntry {
+  char name[32];
+  int64_t launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+struct Pending {
+  int id;
+  cudaEvent_t a, b;
+  double bytes;
+};
+extern std::mutex g_prof_mu;
+extern bool g_prof_on;
+extern std::vector<ProfEntry> g_prof;
+extern std::vector<Pending> g_pending;
+extern std::vector<cudaEvent_t> g_pool;
+
+inline int prof_id(const char* name) {
+  for (size_t i = 0; i < g_prof.size(); ++i)
+    if (strncmp(g_prof[i].name, name, sizeof(g_prof[i].name)) == 0) return (int)i;
+  ProfEntry e;
+  strncpy(e.name, name, sizeof(e.name) - 1);
+  e.name[sizeof(e.name) - 1] = 0;
+  g_prof.push_back(e);
+  return (int)g_prof.size() - 1;
+}
+
+inline cudaEvent_t pool_event() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold completed event pairs into the table (call after a stream synchronisation).
+inline void prof_flush() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  size_t keep = 0;
+  for (size_t i = 0; i < g_pending.size(); ++i) {
+    Pending& p = g_pending[i];
+    float ms = 0.f;
+    if (cudaEventQuery(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_prof[p.id].launches += 1;
+      g_prof[p.id].ms += ms;
+      g_prof[p.id].bytes += p.bytes;
+      g_pool.push_back(p.a);
+      g_pool.push_back(p.b);
+    } else {
+      g_pending[keep++] = p;
+    }
+  }
+  g_pending.resize(keep);
+  cudaGetLastError();
+}
+
+struct ProfScope {
+  bool on;
+  int id = -1;
+  cudaEvent_t a = nullptr;
+  double bytes;
+  cudaStream_t s;
+  ProfScope(const char* name, double b, cudaStream_t st) : on(g_prof_on), bytes(b), s(st) {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    id = prof_id(name);
+    a = pool_event();
+    cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = pool_event();
+    cudaEventRecord(b, s);
+    g_pending.push_back(Pending{id, a, b, bytes});
+  }
+};
+
+#define SVT_CAT2(a, b) a##b
+#define SVT_CAT(a, b) SVT_CAT2(a, b)
+#define SVT_PROF(name, bytes, stream) ProfScope SVT_CAT(svt_prof_, __LINE__)(name, (double)(bytes), stream)
+
+// Algorithmic bytes (what the method must move once) of the main kernel classes.
+inline double spmm_bytes(int64_t nnz, int64_t rows, int64_t cols, int w, int sv) {
+  return (double)nnz * (sv + 4) + 4.0 * (rows + 1) + (double)sv * ((double)cols * w + (double)rows * w);
+}
+inline double update_bytes(int64_t nnz, int64_t m, int64_t n, int k, int sv) {
+  return (double)nnz * (4 + 3 * sv) + 4.0 * (m + 1) + (double)sv * k * (double)(m + n);
+}
+inline double gemm_bytes(int64_t M, int p, int q, int sv, bool reads_c) {
+  return (double)sv * (double)M * (p + q + (reads_c ? q : 0));
+}
+
+constexpr double kExhaustedRel = 1e-7;
+constexpr uint32_t kPowerSeedIter = 0xFFFFFFFFu;
+// Ogita-Aishima steps after the binary32 Jacobi: each squares the eigenvector error
+// (about 1e-7 after Jacobi), so one step reaches binary32-path accuracy and two reach
+// binary64.
+template <typename T>
+constexpr int refine_steps() { return sizeof(T) == 8 ? 2 : 1; }
+
+struct Params {
+  int64_t m, n;
+  int r_cap, t_eff, dt, np, power_steps;
+  double beta, eps_thr0;
+  uint64_t seed;
+};
+
+inline svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params* P) {
+  if (!o) return fail(SVT_ERR_ARG, "null options");
+  if (o->dt <= 0 || o->n_power < 0 || !(o->beta > 0.0 && o->beta < 1.0) || o->power_steps < 1)
+    return fail(SVT_ERR_ARG, "options: need dt > 0, n_power >= 0, 0 < beta < 1, power_steps >= 1");
+  if (o->precision != SVT_FP64 && o->precision != SVT_MIXED_FP32)
+    return fail(SVT_ERR_ARG, "options: unknown precision %d", o->precision);
+  const int64_t mn = std::min(m, n);
+  int64_t cap = o->r_max > 0 ? std::min<int64_t>(mn, o->r_max) : mn;
+  if (cap > 1024)
+    return fail(SVT_ERR_UNSUPPORTED, "rank cap min(m, n, r_max) = %lld exceeds 1024; set r_max",
+                (long long)cap);
+  int64_t t = o->t > 0 ? o->t : (int64_t)std::floor(0.05 * (double)mn);
+  if (t < 1) t = 1;
+  P->m = m; P->n = n; P->r_cap = (int)cap; P->t_eff = (int)std::min<int64_t>(t, 1 << 20);
+  P->dt = o->dt; P->np = o->n_power; P->power_steps = o->power_steps;
+  P->beta = o->beta; P->eps_thr0 = o->eps_thr0; P->seed = o->seed;
+  return SVT_OK;
+}
+
+inline int64_t ld_of(int64_t cols) { return round_up(cols > 0 ? cols : 1, 4); }
+
+namespace {
+template <typename T>
+__global__ void k_scale_cols(int r, int k, const double* __restrict__ Ub, int64_t ldu,
+                             const double* __restrict__ coef, double* __restrict__ out) {
+  const int64_t total = (int64_t)r * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / k), j = (int)(t % k);
+    out[t] = Ub[(int64_t)i * ldu + j] * coef[j];
+  }
+}
+
+__global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ ss,
+                            double* __restrict__ v) {
+  const double inv = 1.0 / sqrt(ss[0]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * inv;
+}
+
+}  // namespace
+
+// Device buffers of one solve (or one R4SVD call).
+template <typename T>
+struct Work {
+  Params P;
+  const svt_pattern* pat = nullptr;
+  cudaStream_t s = nullptr;
+  int wmax = 1;
+  int64_t ldq = 0, ldb = 0, ldw = 0, ldk = 0;
+  T *Qa = nullptr, *Qb = nullptr;   // m x ldq (basis / recycled U, ping-pong)
+  T *Bt = nullptr;                  // n x ldb
+  T *Om = nullptr, *Z = nullptr;    // n x ldw
+  T *X = nullptr, *X2 = nullptr;    // m x ldw
+  T *Wk = nullptr;                  // n x ldk (V_K scaled by sigma - tau, or V)
+  T *y_csc = nullptr;               // nnz
+  double *G = nullptr, *Ub = nullptr, *lam = nullptr, *Gs = nullptr;
+  double *Gx = nullptr, *Rm = nullptr, *Rinv = nullptr, *cwork = nullptr, *Tsm = nullptr;
+  double *coef = nullptr, *part = nullptr, *eigw = nullptr, *dsc = nullptr, *colss = nullptr;
+  double *pv = nullptr, *pu = nullptr, *pw = nullptr;  // power-iteration vectors
+  unsigned* flags = nullptr;
+  void* spmm_scr = nullptr;         // partial rows of the entry-chunked SpMM
+
+  void layout(Arena& a) {
+    const int64_t m = P.m, n = P.n, z = pat->nnz;
+    const int rc = P.r_cap;
+    wmax = std::max(std::min(P.t_eff, rc), std::min(P.dt, rc));
+    ldq = ld_of(rc); ldb = ld_of(rc); ldw = ld_of(wmax); ldk = ld_of(rc);
+    Qa = a.take<T>(m * ldq); Qb = a.take<T>(m * ldq);
+    Bt = a.take<T>(n * ldb);
+    Om = a.take<T>(n * ldw); Z = a.take<T>(n * ldw);
+    X = a.take<T>(m * ldw); X2 = a.take<T>(m * ldw);
+    Wk = a.take<T>(n * ldk);
+    y_csc = a.take<T>(z);
+    G = a.take<double>((int64_t)rc * rc);
+    Ub = a.take<double>((int64_t)rc * rc);
+    lam = a.take<double>(rc);
+    Gs = a.take<double>((int64_t)rc * wmax);
+    Gx = a.take<double>((int64_t)wmax * wmax);
+    Rm = a.take<double>((int64_t)wmax * wmax);
+    Rinv = a.take<double>((int64_t)wmax * wmax);
+    cwork = a.take<double>((int64_t)wmax * wmax);
+    Tsm = a.take<double>((int64_t)rc * rc);
+    coef = a.take<double>(rc);
+    size_t pe = reduce_scratch();
+    pe = std::max(pe, gemm_tn_scratch(m, rc, wmax));
+    pe = std::max(pe, gemm_tn_scratch(m, wmax, wmax));
+    pe = std::max(pe, gemm_tn_scratch(n, rc, rc));
+    pe = std::max(pe, colsumsq_scratch(std::max(m, n), std::max(wmax, rc)));
+    part = a.take<double>(pe);
+    eigw = a.take<double>(eig_scratch(rc));
+    dsc = a.take<double>(16);
+    colss = a.take<double>(std::max(wmax, rc));
+    pv = a.take<double>(n); pw = a.take<double>(n); pu = a.take<double>(m);
+    flags = a.take<unsigned>(4);
+    const size_t sb = std::max(spmm_scratch_bytes(z, std::max(wmax, rc), (int)sizeof(T)),
+                               spmm_scratch_bytes(z, 1, 8));
+    spmm_scr = a.take<char>(sb);
+  }
+};
+
+template <typename T>
+svt_status read_flags(Work<T>& W, unsigned* out) {
+  SVT_CUDA(cudaMemcpyAsync(out, W.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  return SVT_OK;
+}
+
+// Sum of squares of columns [c0, c0+w) of an M x w block, summed on the host in column order.
+template <typename T>
+svt_status block_sumsq(Work<T>& W, int64_t M, int w, const T* X, int64_t ldx, double* out,
+                       double* maxcol = nullptr) {
+  std::vector<double> h(w > 0 ? w : 1);
+  if (w <= 0) { *out = 0.0; if (maxcol) *maxcol = 0.0; return SVT_OK; }
+  SVT_TRY(colsumsq<T>(M, w, X, ldx, W.colss, W.part, W.s));
+  SVT_CUDA(cudaMemcpyAsync(h.data(), W.colss, w * sizeof(double), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  double s = 0.0, mx = 0.0;
+  for (int c = 0; c < w; ++c) { s += h[c]; mx = std::max(mx, h[c]); }
+  *out = s;
+  if (maxcol) *maxcol = std::sqrt(mx);
+  return SVT_OK;
+}
+
+struct R4Out {
+  int r = 0, blocks = 0;
+  bool exhausted = false;
+  double eps = 0.0, normB = 0.0;
+  std::vector<double> sigma;  // descending, r entries
+};
+
+// Algorithm 3 (Algorithm 2 when s == 0).  Q holds the recycled basis in columns [0, s);
+// new blocks are appended in place.  On return U = Q U_B is written to Unew (m x ldq),
+// Bt (n x r) = Y^T Q, W.Ub = U_B, sigma on the host.
+template <typename T>
+svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, double normY2,
+                     double eps_thr, uint32_t iter, T* Unew, R4Out* o) {
+  const Params& P = W.P;
+  const svt_pattern* p = W.pat;
+  const int64_t m = P.m, n = P.n;
+  cudaStream_t st = W.s;
+  int r = s;
+  double normB = 0.0;
+  const int sv = (int)sizeof(T);
+  const int64_t z = p->nnz;
+  if (s > 0) {
+    {
+      SVT_PROF("spmm_csc_recycled", spmm_bytes(z, n, m, s, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, W.spmm_scr, z, st, p->chunk_row_csc)));
+    }
+    SVT_TRY(block_sumsq<T>(W, n, s, W.Bt, W.ldb, &normB));
+  }
+  auto eps_of = [&](double nb) { return normY2 > 0.0 ? (normY2 - nb) / normY2 : 0.0; };
+  double eps = eps_of(normB);
+  bool first = (s == 0);
+  int blocks = 0;
+  bool exhausted = false;
+  while ((first || eps > eps_thr) && r < P.r_cap) {
+    const int w = first ? std::min(P.t_eff, P.r_cap) : std::min(P.dt, P.r_cap - r);
+    {
+      SVT_PROF("gaussian", (double)sv * n * w, st);
+      SVT_TRY(launch_gaussian<T>(P.seed, iter, (uint32_t)blocks, n, w, W.Om, W.ldw, st));
+    }
+    ++blocks;
+    {
+      SVT_PROF("spmm_csr", spmm_bytes(z, m, n, w, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, W.spmm_scr, z, st, p->chunk_row_csr)));
+    }
+    for (int it = 0; it < P.np; ++it) {
+      SVT_PROF("spmm_power", spmm_bytes(z, n, m, w, sv) + spmm_bytes(z, m, n, w, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, W.X, W.ldw, w, W.Z, W.ldw, W.spmm_scr, z, st, p->chunk_row_csc)));
+      SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Z, W.ldw, w, W.X, W.ldw, W.spmm_scr, z, st, p->chunk_row_csr)));
+    }
+    double ssum = 0.0, scale = 0.0;
+    SVT_TRY(block_sumsq<T>(W, m, w, W.X, W.ldw, &ssum, &scale));
+    if (r > 0) {
+      for (int pass = 0; pass < 2; ++pass) {  // X <- X - Q (Q^T X), twice
+        SVT_PROF("orthogonalise", gemm_bytes(m, r, w, sv, false) + gemm_bytes(m, r, w, sv, true), st);
+        SVT_TRY((gemm_tn<T, T>(m, r, w, Q, W.ldq, W.X, W.ldw, W.Gs, w, W.part, st)));
+        SVT_TRY((gemm_nn<T, T>(m, r, w, -1.0, Q, W.ldq, W.Gs, w, 1.0, W.X, W.ldw, W.X2, W.ldw, st)));
+        std::swap(W.X, W.X2);
+      }
+    }
+    // Cholesky-QR, twice: X = Q' R
+    SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
+    {
+      SVT_PROF("cholqr", gemm_bytes(m, w, 0, sv, false), st);
+      SVT_TRY((gemm_tn<T, T>(m, w, w, W.X, W.ldw, W.X, W.ldw, W.Gx, w, W.part, st)));
+      SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 0, W.flags, st));
+    }
+    double dmin = 0.0;
+    unsigned fl = 0;
+    SVT_CUDA(cudaMemcpyAsync(&dmin, W.dsc + 0, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SVT_TRY(read_flags(W, &fl));
+    if (scale == 0.0 || (fl & FLAG_CHOLESKY) || !(dmin > kExhaustedRel * scale)) {
+      exhausted = true;
+      break;
+    }
+    {
+      SVT_PROF("cholqr", gemm_bytes(m, w, w, sv, false) + gemm_bytes(m, w, 0, sv, false), st);
+      SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X, W.ldw, W.Rinv, w, 0.0, nullptr, 0, W.X2, W.ldw, st)));
+      SVT_TRY((gemm_tn<T, T>(m, w, w, W.X2, W.ldw, W.X2, W.ldw, W.Gx, w, W.part, st)));
+      SVT_TRY(chol_inv(w, W.Gx, w, W.Rm, W.Rinv, W.cwork, W.dsc + 1, W.flags, st));
+    }
+    SVT_TRY(read_flags(W, &fl));
+    if (fl & FLAG_CHOLESKY) return fail(SVT_ERR_NUMERIC, "R4SVD: Cholesky-QR breakdown in block %d", blocks);
+    {
+      SVT_PROF("cholqr", gemm_bytes(m, w, w, sv, false), st);
+      SVT_TRY((gemm_nn<T, T>(m, w, w, 1.0, W.X2, W.ldw, W.Rinv, w, 0.0, nullptr, 0, Q + r, W.ldq, st)));
+    }
+    // B'^T = Y^T Q'
+    {
+      SVT_PROF("spmm_csc", spmm_bytes(z, n, m, w, sv), st);
+      SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q + r, W.ldq, w, W.Bt + r, W.ldb, W.spmm_scr, z, st, p->chunk_row_csc)));
+    }
+    double nb = 0.0;
+    SVT_TRY(block_sumsq<T>(W, n, w, W.Bt + r, W.ldb, &nb));
+    normB += nb;
+    r += w;
+    eps = eps_of(normB);
+    first = false;
+  }
+  o->r = r; o->blocks = blocks; o->exhausted = exhausted; o->eps = eps; o->normB = normB;
+  o->sigma.assign(r, 0.0);
+  if (r == 0) return SVT_OK;
+  // svt(B): eigen-decomposition of B B^T = (B^T)^T B^T
+  {
+    SVT_PROF("gram_B", gemm_bytes(n, r, 0, sv, false), st);
+    SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
+  }
+  {
+    SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
+    SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2)));
+  }
+  {
+    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
+  }
+  std::vector<double> lam(r);
+  SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // U = Q U_B (all r columns are recycled)
+  {
+    SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
+    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+  }
+  SVT_CUDA(cudaStreamSynchronize(st));
+  prof_flush();
+  if (g_prof_on) {  // sweep count of the binary32 Jacobi stage, kept as a pseudo-entry
+    int sweeps = 0;
+    if (cudaMemcpy(&sweeps, W.flags + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      const int id = prof_id("jacobi_sweeps");
+      g_prof[id].launches += 1;
+      g_prof[id].bytes += sweeps;
+    }
+  }
+  for (int j = 0; j < r; ++j) {
+    if (!std::isfinite(lam[j])) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
+    o->sigma[j] = std::sqrt(std::max(lam[j], 0.0));
+  }
+  return SVT_OK;
+}
+
+// Wk (n x k) = Bt (n x r) * Ub[:, :k] diag(coef)
+template <typename T>
+svt_status scaled_right(Work<T>& W, int r, int k, const std::vector<double>& coef) {
+  if (k <= 0) return SVT_OK;
+  SVT_CUDA(cudaMemcpyAsync(W.coef, coef.data(), k * sizeof(double), cudaMemcpyHostToDevice, W.s));
+  const int64_t total = (int64_t)r * k;
+  k_scale_cols<T><<<(int)std::min<int64_t>(ceil_div(total, 256), 1024), 256, 0, W.s>>>(
+      r, k, W.Ub, r, W.coef, W.Tsm);
+  SVT_LAUNCH_CHECK();
+  SVT_PROF("lift_V", gemm_bytes(W.P.n, r, k, (int)sizeof(T), false), W.s);
+  SVT_TRY((gemm_nn<T, T>(W.P.n, r, k, 1.0, W.Bt, W.ldb, W.Tsm, k, 0.0, nullptr, 0, W.Wk, W.ldk, W.s)));
+  return SVT_OK;
+}
+
+// Copy the first k columns of a device T matrix into caller memory (double, ld = cap).
+template <typename T>
+svt_status export_cols(Work<T>& W, int64_t rows, int k, const T* src, int64_t lds, double* dst,
+                       int cap) {
+  if (rows <= 0 || cap <= 0) return SVT_OK;
+  const bool dev = is_device_pointer(dst);
+  if (dev) {
+    SVT_CUDA(cudaMemsetAsync(dst, 0, rows * cap * sizeof(double), W.s));
+    SVT_TRY((copy_convert<T, double>(rows, k, src, lds, dst, cap, W.s)));
+    return SVT_OK;
+  }
+  DeviceBlock tmp;
+  SVT_TRY(tmp.alloc(rows * cap * sizeof(double), W.s));
+  double* d = (double*)tmp.ptr;
+  SVT_CUDA(cudaMemsetAsync(d, 0, rows * cap * sizeof(double), W.s));
+  SVT_TRY((copy_convert<T, double>(rows, k, src, lds, d, cap, W.s)));
+  SVT_CUDA(cudaMemcpyAsync(dst, d, rows * cap * sizeof(double), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  return SVT_OK;
+}
+
+
+}  // namespace svt

@@ -137,7 +137,17 @@ k_spmm_fixup(int64_t nchunks, int64_t C, const int32_t* __restrict__ ptr,
   const int64_t c_last = ((int64_t)ptr[r + 1] - 1) / C;
   for (int c = lane; c < w; c += 32) {
     TD s = part[(2 * chunk + 1) * ldp + c];
-    for (int64_t k = chunk + 1; k <= c_last; ++k) s += part[(2 * k) * ldp + c];
+    // a row can span hundreds of chunks: issue eight independent loads per step and
+    // add them in chunk order (the same order as one at a time)
+    int64_t k = chunk + 1;
+    for (; k + 8 <= c_last + 1; k += 8) {
+      TD v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = part[(2 * (k + j)) * ldp + c];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s += v[j];
+    }
+    for (; k <= c_last; ++k) s += part[(2 * k) * ldp + c];
     out[(int64_t)r * ldo + c] = s;
   }
 }

@@ -5,8 +5,12 @@
 // One warp owns a CSR row p; its lanes take the row's entries in turn, evaluate
 // x_pq = U[p, :] . W[q, :], d = A_pq - x_pq, update Y_pq += delta d and accumulate
 // sum d^2 (the residual of Algorithm 4), sum |d| (MAE) and sum Y_new^2 (the next
-// ||Y||_F^2 of R4SVD) in binary64.  Block partials are summed in block order by a
-// second pass, so the sums are reproducible.
+// ||Y||_F^2 of R4SVD).  Binary64 data sums in binary64; binary32 data sums in pairs of
+// binary32 values with error-free updates, which keeps about 2^-44 of relative accuracy
+// on the binary32 pipes (binary64 arithmetic runs at a small fraction of the binary32
+// rate on this GPU, and one binary64 operation per entry already bounds the kernel).
+// Block partials are summed in block order by a second pass, so the sums are
+// reproducible.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -20,6 +24,38 @@ namespace {
 constexpr int kRedBlocksPerSm = 8;
 
 int red_blocks() { return num_sms() * kRedBlocksPerSm; }
+
+template <typename T>
+struct SumAcc;
+
+template <>
+struct SumAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_sq(double x) { s = fma(x, x, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// hi + lo holds the sum.  Knuth's TwoSum gives the exact error of hi + p, and fma gives
+// the exact error of a rounded product; the intrinsics keep the compiler from fusing
+// the steps that must round separately.
+template <>
+struct SumAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add2(float p, float e) {
+    const float t = __fadd_rn(hi, p);
+    const float z = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+    hi = t;
+  }
+  __device__ __forceinline__ void add(float x) { add2(x, 0.f); }
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = __fmul_rn(x, x);
+    add2(p, fmaf(x, x, -p));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 template <typename T, int VEC>
 __device__ __forceinline__ void load_v(const T* p, T (&v)[VEC]) {
@@ -54,7 +90,7 @@ k_sampled_update(int64_t nnz, int64_t C, int64_t nchunks, const int32_t* __restr
   const int grp = lane / G, gl = lane % G;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double s_d2 = 0.0, s_abs = 0.0, s_y2 = 0.0;
+  SumAcc<T> acc_d2, acc_abs, acc_y2;
   bool bad = false;
   for (int64_t chunk = wid; chunk < nchunks; chunk += nw) {
     const int64_t beg = chunk * C;
@@ -128,23 +164,30 @@ k_sampled_update(int64_t nnz, int64_t C, int64_t nchunks, const int32_t* __restr
       for (int j = 0; j < UNR; ++j)
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) px[j] += __shfl_xor_sync(0xffffffffu, px[j], o);
-      // 5. residual and dual update
+      // 5. residual and dual update: lane j0 + l of a group takes entry j0 + l, so the
+      //    group's UNR entries finish in one instruction stream
 #pragma unroll
-      for (int j = 0; j < UNR; ++j) {
-        if (v[j] && gl == 0) {
-          const T d = av[j] - px[j];
-          const T yn = fma(delta, d, yv[j]);
-          y[e[j]] = yn;
-          const double dd = (double)d, yy = (double)yn;
-          s_d2 = fma(dd, dd, s_d2);
-          s_abs += fabs(dd);
-          s_y2 = fma(yy, yy, s_y2);
-          bad |= !isfinite(yy);
+      for (int j0 = 0; j0 < UNR; j0 += G) {
+        T xs = T(0), as = T(0), ys = T(0);
+        int64_t es = 0;
+        bool vs = false;
+#pragma unroll
+        for (int j = j0; j < UNR && j < j0 + G; ++j)
+          if (gl == j - j0) { xs = px[j]; as = av[j]; ys = yv[j]; es = e[j]; vs = v[j]; }
+        if (vs) {
+          const T d = as - xs;
+          const T yn = fma(delta, d, ys);
+          y[es] = yn;
+          acc_d2.add_sq(d);
+          acc_abs.add(fabs(d));
+          acc_y2.add_sq(yn);
+          bad |= !isfinite(yn);
         }
       }
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NONFINITE);
+  double s_d2 = acc_d2.value(), s_abs = acc_abs.value(), s_y2 = acc_y2.value();
   s_d2 = block_sum(s_d2, red);
   __syncthreads();
   s_abs = block_sum(s_abs, red);

@@ -60,3 +60,28 @@ def test_argument_validation_without_gpu(lib):
     assert b"tau" in lib.svt_last_error()
     h = C.c_void_p()
     assert lib.svt_pattern_create(-1, 3, 0, None, None, None, C.byref(h)) == L.SVT_ERR_ARG
+
+
+def test_unrolled_params_defaults_and_validation(lib):
+    assert C.sizeof(L.UnrolledParams) == 4 * 4 + 2 * 8
+    assert C.sizeof(L.UnrolledInfo) == 8 * 4 + 3 * 8
+    up = L.UnrolledParams()
+    lib.svt_unrolled_default_params(C.byref(up), L.SVT_FP64)
+    assert (up.steps, up.checkpoint_every, up.cg_maxit, up.ritz_maxit) == (20, 5, 1000, 100)
+    assert up.cg_tol == 1e-10 and up.ritz_tol == 1e-11
+    lib.svt_unrolled_default_params(C.byref(up), L.SVT_MIXED_FP32)
+    assert up.cg_tol == 1e-6 and up.ritz_tol == 2e-6
+    o = L.Options()
+    lib.svt_default_options(C.byref(o))
+    info = L.UnrolledInfo()
+    # rejected before any device work: no held-out set, then a bad checkpoint interval
+    idx = (C.c_int32 * 1)(0)
+    val = (C.c_double * 1)(1.0)
+    st = lib.svt_unrolled_grad(2, 2, 1, idx, idx, val, 0, idx, idx, val, 1.0, 1.0, None, C.byref(o),
+                               None, None, None, C.byref(info))
+    assert st == L.SVT_ERR_ARG
+    lib.svt_unrolled_default_params(C.byref(up), L.SVT_FP64)
+    up.checkpoint_every = 0
+    st = lib.svt_unrolled_grad(2, 2, 1, idx, idx, val, 1, idx, idx, val, 1.0, 1.0, C.byref(up),
+                               C.byref(o), None, None, None, C.byref(info))
+    assert st == L.SVT_ERR_ARG and b"checkpoint_every" in lib.svt_last_error()
