@@ -692,13 +692,13 @@ svt_status unrolled_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     if (cap) {  // A - X on Lambda: the sampled update of a zero vector with step 1
       SVT_CUDA(cudaMemsetAsync(cap->d, 0, nnz * sizeof(T), st));
       SVT_TRY(sampled_update<T>(pl, S.Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, cap->d, 1.0, part3, W.part,
-                                W.flags, st));
+                                W.flags, st, true));
     }
     io->r = ro.r; io->k = k;
     io->sigma.assign(ro.sigma.begin(), ro.sigma.begin() + k);
     if (!update_y) return SVT_OK;
     SVT_TRY(sampled_update<T>(pl, S.Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
-                              W.part, W.flags, st));
+                              W.part, W.flags, st, true));
     double sums[3];
     SVT_CUDA(cudaMemcpyAsync(sums, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaStreamSynchronize(st));

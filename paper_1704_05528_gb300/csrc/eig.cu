@@ -257,13 +257,15 @@ k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ 
   __shared__ double key[1024];
   __shared__ int idx[1024];
   const int t = threadIdx.x;
+  int P = 2;  // bitonic network over the next power of two >= r
+  while (P < r) P <<= 1;
   key[t] = t < r ? lam_in[t] : -INFINITY;
   idx[t] = t;
   __syncthreads();
-  for (int k = 2; k <= 1024; k <<= 1) {
+  for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       const int ixj = t ^ j;
-      if (ixj > t) {
+      if (ixj > t && ixj < P) {
         const bool desc = (t & k) == 0;
         const double a = key[t], b = key[ixj];
         const int ia = idx[t], ib = idx[ixj];
@@ -277,10 +279,9 @@ k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ 
     }
   }
   if (t < r) lam_out[t] = key[t];
-  for (int64_t e = t; e < (int64_t)r * r; e += blockDim.x) {
-    const int a = (int)(e / r), j = (int)(e % r);
-    Ub[(int64_t)a * ldu + j] = X[(int64_t)a * r + idx[j]];
-  }
+  // row a of Ub, column j: warp w takes rows w, w + 32, ...; lanes take columns
+  for (int a = t >> 5; a < r; a += blockDim.x >> 5)
+    for (int j = t & 31; j < r; j += 32) Ub[(int64_t)a * ldu + j] = X[(int64_t)a * r + idx[j]];
 }
 
 }  // namespace

@@ -87,9 +87,11 @@ template <typename TS, typename T>
 svt_status gather_convert(int64_t count, const int32_t* src, const TS* vals, T* a_csr,
                           cudaStream_t s);
 // Sampled shrinkage + update over CSR rows; out3 (device) = {sum d^2, sum |d|, sum y^2}.
+// w_pad_zero: columns k .. round_up(k, 4) - 1 of W hold zeros (the solver's own W), so
+// whole vectors of a row multiply without per-element tests.
 template <typename T>
 svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W,
                           int64_t ldw, int k, const T* a, T* y, double delta, double* out3,
-                          double* part, unsigned* flags, cudaStream_t s);
+                          double* part, unsigned* flags, cudaStream_t s, bool w_pad_zero = false);
 
 }  // namespace svt

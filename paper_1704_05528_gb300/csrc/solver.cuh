@@ -159,14 +159,15 @@ inline svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params
 inline int64_t ld_of(int64_t cols) { return round_up(cols > 0 ? cols : 1, 4); }
 
 namespace {
+// out (r x kp, ld kp) = Ub[:, :k] diag(coef), with zero columns k .. kp-1
 template <typename T>
-__global__ void k_scale_cols(int r, int k, const double* __restrict__ Ub, int64_t ldu,
+__global__ void k_scale_cols(int r, int k, int kp, const double* __restrict__ Ub, int64_t ldu,
                              const double* __restrict__ coef, double* __restrict__ out) {
-  const int64_t total = (int64_t)r * k;
+  const int64_t total = (int64_t)r * kp;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / k), j = (int)(t % k);
-    out[t] = Ub[(int64_t)i * ldu + j] * coef[j];
+    const int i = (int)(t / kp), j = (int)(t % kp);
+    out[t] = j < k ? Ub[(int64_t)i * ldu + j] * coef[j] : 0.0;
   }
 }
 
@@ -220,7 +221,7 @@ struct Work {
     Rm = a.take<double>((int64_t)wmax * wmax);
     Rinv = a.take<double>((int64_t)wmax * wmax);
     cwork = a.take<double>((int64_t)wmax * wmax);
-    Tsm = a.take<double>((int64_t)rc * rc);
+    Tsm = a.take<double>((int64_t)rc * ld_of(rc));
     coef = a.take<double>(rc);
     size_t pe = reduce_scratch();
     pe = std::max(pe, gemm_tn_scratch(m, rc, wmax));
@@ -401,17 +402,20 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   return SVT_OK;
 }
 
-// Wk (n x k) = Bt (n x r) * Ub[:, :k] diag(coef)
+// Wk (n x k) = Bt (n x r) * Ub[:, :k] diag(coef).  Columns k .. round_up(k, 4) - 1 of Wk
+// are written as exact zeros (zero coefficients times the finite Bt), so the sampled update
+// may read them in whole vectors without masking.
 template <typename T>
 svt_status scaled_right(Work<T>& W, int r, int k, const std::vector<double>& coef) {
   if (k <= 0) return SVT_OK;
+  const int kp = (int)round_up(k, 4);
   SVT_CUDA(cudaMemcpyAsync(W.coef, coef.data(), k * sizeof(double), cudaMemcpyHostToDevice, W.s));
-  const int64_t total = (int64_t)r * k;
+  const int64_t total = (int64_t)r * kp;
   k_scale_cols<T><<<(int)std::min<int64_t>(ceil_div(total, 256), 1024), 256, 0, W.s>>>(
-      r, k, W.Ub, r, W.coef, W.Tsm);
+      r, k, kp, W.Ub, r, W.coef, W.Tsm);
   SVT_LAUNCH_CHECK();
   SVT_PROF("lift_V", gemm_bytes(W.P.n, r, k, (int)sizeof(T), false), W.s);
-  SVT_TRY((gemm_nn<T, T>(W.P.n, r, k, 1.0, W.Bt, W.ldb, W.Tsm, k, 0.0, nullptr, 0, W.Wk, W.ldk, W.s)));
+  SVT_TRY((gemm_nn<T, T>(W.P.n, r, kp, 1.0, W.Bt, W.ldb, W.Tsm, kp, 0.0, nullptr, 0, W.Wk, W.ldk, W.s)));
   return SVT_OK;
 }
 

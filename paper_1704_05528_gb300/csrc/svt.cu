@@ -257,7 +257,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     {
       SVT_PROF("sampled_update", update_bytes(nnz, m, n, k, (int)sizeof(T)), st);
       SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
-                                W.part, W.flags, st));
+                                W.part, W.flags, st, true));
     }
     double sums[3];
     unsigned fl = 0;

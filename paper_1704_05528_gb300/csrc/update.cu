@@ -78,7 +78,7 @@ __device__ __forceinline__ void load_v(const T* p, T (&v)[VEC]) {
 // reloaded when it changes) and multiplies them with the same slices of W[q, :]; a
 // shuffle tree over the group gives x_pq.  Loop trip counts are uniform across the warp
 // so every lane reaches the shuffles.
-template <typename T, int VEC, int G, int MAXV, int UNR>
+template <typename T, int VEC, int G, int MAXV, int UNR, bool WPAD>
 __global__ void __launch_bounds__(256)
 k_sampled_update(int64_t nnz, int64_t C, int64_t nchunks, const int32_t* __restrict__ csr_row,
                  const int32_t* __restrict__ col_idx, const T* __restrict__ U, int64_t ldu,
@@ -154,8 +154,11 @@ k_sampled_update(int64_t nnz, int64_t C, int64_t nchunks, const int32_t* __restr
           for (int t = 0; t < MAXV; ++t) {
             const int c0 = (gl + t * G) * VEC;
 #pragma unroll
-            for (int bb = 0; bb < VEC; ++bb)
-              if (c0 + bb < k) px[j] = fma(u[t][bb], wx[j][t][bb], px[j]);
+            for (int bb = 0; bb < VEC; ++bb) {
+              // WPAD: W's columns up to the next vector boundary are finite (zeros) and u
+              // is zero there, so whole vectors multiply without a per-element test
+              if (WPAD || c0 + bb < k) px[j] = fma(u[t][bb], wx[j][t][bb], px[j]);
+            }
           }
         }
       }
@@ -280,7 +283,7 @@ svt_status gather_convert(int64_t count, const int32_t* src, const TS* vals, T* 
   return SVT_OK;
 }
 
-template <typename T, int VEC, int G, int MAXV>
+template <typename T, int VEC, int G, int MAXV, bool WPAD>
 svt_status run_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W, int64_t ldw,
                       int k, const T* a, T* y, double delta, double* part, unsigned* flags,
                       cudaStream_t s) {
@@ -288,20 +291,20 @@ svt_status run_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W,
   const int64_t C = chunk_size(p->nnz > 0 ? p->nnz : 1);
   const int64_t nchunks = ceil_div(p->nnz, C);
   constexpr int UNR = (MAXV * VEC <= 16) ? 2 : 1;
-  k_sampled_update<T, VEC, G, MAXV, UNR><<<blocks, 256, 0, s>>>(p->nnz, C, nchunks, p->csr_row,
+  k_sampled_update<T, VEC, G, MAXV, UNR, WPAD><<<blocks, 256, 0, s>>>(p->nnz, C, nchunks, p->csr_row,
                                                                 p->col_idx, U, ldu, W, ldw, k, a, y,
                                                                 (T)delta, part, flags);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
 
-template <typename T, int VEC>
+template <typename T, int VEC, bool WPAD>
 svt_status dispatch_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W, int64_t ldw,
                            int k, const T* a, T* y, double delta, double* part, unsigned* flags,
                            cudaStream_t s) {
   const int nv = (int)ceil_div(k > 0 ? k : 1, VEC);
   // at most 4 vectors per lane, as few lanes per entry as that allows
-#define SVT_RUN(G, MV) return run_update<T, VEC, G, MV>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)
+#define SVT_RUN(G, MV) return run_update<T, VEC, G, MV, WPAD>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)
   if (nv <= 4) SVT_RUN(1, 4);
   if (nv <= 8) SVT_RUN(2, 4);
   if (nv <= 16) SVT_RUN(4, 4);
@@ -317,14 +320,18 @@ svt_status dispatch_update(const svt_pattern* p, const T* U, int64_t ldu, const 
 template <typename T>
 svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W,
                           int64_t ldw, int k, const T* a, T* y, double delta, double* out3,
-                          double* part, unsigned* flags, cudaStream_t s) {
+                          double* part, unsigned* flags, cudaStream_t s, bool w_pad_zero) {
   if (k > 1024) return fail(SVT_ERR_UNSUPPORTED, "sampled update: k = %d exceeds 1024", k);
   constexpr int V = sizeof(T) == 4 ? 4 : 2;
   const bool aligned = (reinterpret_cast<uintptr_t>(U) % 16 == 0) && (ldu % V == 0) &&
-                       (reinterpret_cast<uintptr_t>(W) % 16 == 0) && (ldw % V == 0);
+                       (reinterpret_cast<uintptr_t>(W) % 16 == 0) && (ldw % V == 0) &&
+                       (!w_pad_zero || ldw >= round_up(k, 4));
   if (p->nnz > 0) {
-    if (aligned) SVT_TRY((dispatch_update<T, V>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
-    else SVT_TRY((dispatch_update<T, 1>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
+    if (aligned && w_pad_zero)
+      SVT_TRY((dispatch_update<T, V, true>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
+    else if (aligned)
+      SVT_TRY((dispatch_update<T, V, false>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
+    else SVT_TRY((dispatch_update<T, 1, false>(p, U, ldu, W, ldw, k, a, y, delta, part, flags, s)));
   } else {
     SVT_CUDA(cudaMemsetAsync(part, 0, 3 * red_blocks() * sizeof(double), s));
   }
@@ -343,9 +350,9 @@ template svt_status gather_convert<float, float>(int64_t, const int32_t*, const 
                                                  cudaStream_t);
 template svt_status sampled_update<double>(const svt_pattern*, const double*, int64_t,
                                            const double*, int64_t, int, const double*, double*,
-                                           double, double*, double*, unsigned*, cudaStream_t);
+                                           double, double*, double*, unsigned*, cudaStream_t, bool);
 template svt_status sampled_update<float>(const svt_pattern*, const float*, int64_t, const float*,
                                           int64_t, int, const float*, float*, double, double*,
-                                          double*, unsigned*, cudaStream_t);
+                                          double*, unsigned*, cudaStream_t, bool);
 
 }  // namespace svt

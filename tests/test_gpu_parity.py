@@ -139,6 +139,42 @@ def test_sampled_update(svt, torch_mod, k):
     assert math.isclose(sums[2], float(np.sum(y_ref * y_ref)), rel_tol=1e-12)
 
 
+@pytest.mark.parametrize("k", [4, 60, 100, 128, 132, 7])
+def test_sampled_update_mixed(svt, torch_mod, k):
+    """Binary32 update on a pattern with heavy columns (40 columns holding 24,000 entries),
+    an empty column range and a narrow last block of columns; k = 7 has unaligned rows
+    (scalar loads), the others take the float4 path."""
+    rng = np.random.default_rng(7 + k)
+    m, n = 3001, 1300
+    heavy = rng.choice(m * 40, size=24000, replace=False)
+    other_cols = np.setdiff1d(np.arange(40, n), np.arange(512, 768))
+    flat_o = rng.choice(m * other_cols.size, size=36000, replace=False)
+    rows = np.concatenate([heavy // 40, flat_o // other_cols.size]).astype(np.int32)
+    cols = np.concatenate([heavy % 40, other_cols[flat_o % other_cols.size]]).astype(np.int32)
+    perm = rng.permutation(rows.size)
+    rows, cols = rows[perm], cols[perm]
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    f32 = lambda x: np.asarray(x, dtype=np.float32)
+    U = f32(rng.standard_normal((m, k)))
+    Wm = f32(rng.standard_normal((n, k)))
+    a = f32(rng.standard_normal(ref_p.nnz))
+    y0 = f32(rng.standard_normal(ref_p.nnz))
+    delta = 1.7
+    x = oracle.sampled_product(U.astype(np.float64), np.ones(k), Wm.astype(np.float64),
+                               ref_p.csr_rows(), ref_p.col_idx)
+    d = a.astype(np.float64) - x
+    y_ref = y0.astype(np.float64) + delta * d
+    y_dev = torch_mod.from_numpy(y0.copy()).cuda()
+    sums = svt.sampled_update(P, torch_mod.from_numpy(U), torch_mod.from_numpy(Wm),
+                              torch_mod.from_numpy(a), y_dev, delta, precision="mixed")
+    got = y_dev.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - y_ref)) < 1e-5 * (1.0 + np.sqrt(k)) * delta
+    assert math.isclose(sums[0], float(np.sum(d * d)), rel_tol=1e-5)
+    assert math.isclose(sums[1], float(np.sum(np.abs(d))), rel_tol=1e-5)
+    assert math.isclose(sums[2], float(np.sum(y_ref * y_ref)), rel_tol=1e-5)
+
+
 # ------------------------------------------------------------------------ R4SVD
 def _sigma_close(got, ref, tol):
     got = np.asarray(got)
