@@ -180,69 +180,76 @@ k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* g
   if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
-// C = op(A) B + beta Cin for r x r row-major binary64 matrices (op(A) = A or A^T), one
-// 8 x 8 output tile per block: binary64 runs at a small fraction of the binary32 rate, so
-// small tiles spread an r = 100 product over all SMs instead of a third of them.
+// C (M x N) = op(A) (M x K) B (K x N) + beta Cin for small row-major binary64 matrices
+// (op(A) = A or A^T), one 8 x 8 output tile per block: binary64 runs at a small fraction
+// of the binary32 rate, so small tiles spread an r = 100 product over all SMs.
 constexpr int kSgTile = 8;
 
 template <bool TRANS_A>
 __global__ void __launch_bounds__(kSgTile * kSgTile)
-k_small_gemm(int r, const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
-             double beta, const double* __restrict__ Cin, double* __restrict__ C) {
+k_small_gemm(int M, int N, int K, const double* __restrict__ A, int64_t lda,
+             const double* __restrict__ B, int64_t ldb, double beta, const double* Cin,
+             int64_t ldcin, double* C, int64_t ldc) {
   constexpr int T = kSgTile;
   __shared__ double As[T][T + 1];
   __shared__ double Bs[T][T + 1];
   const int tx = threadIdx.x % T, ty = threadIdx.x / T;
   const int i = blockIdx.y * T + ty, j = blockIdx.x * T + tx;
   double acc = 0.0;
-  for (int k0 = 0; k0 < r; k0 += T) {
+  for (int k0 = 0; k0 < K; k0 += T) {
     const int ka = k0 + tx, kb = k0 + ty;
     if (TRANS_A) {
       // op(A)[i][k] = A[k][i]: load rows k0.. of A, columns blockIdx.y*T ..
       const int ia = blockIdx.y * T + tx, kk = k0 + ty;
-      As[tx][ty] = (ia < r && kk < r) ? A[(int64_t)kk * lda + ia] : 0.0;
+      As[tx][ty] = (ia < M && kk < K) ? A[(int64_t)kk * lda + ia] : 0.0;
     } else {
-      As[ty][tx] = (i < r && ka < r) ? A[(int64_t)i * lda + ka] : 0.0;
+      As[ty][tx] = (i < M && ka < K) ? A[(int64_t)i * lda + ka] : 0.0;
     }
-    Bs[ty][tx] = (kb < r && j < r) ? B[(int64_t)kb * r + j] : 0.0;
+    Bs[ty][tx] = (kb < K && j < N) ? B[(int64_t)kb * ldb + j] : 0.0;
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < T; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
     __syncthreads();
   }
-  if (i < r && j < r) {
-    const int64_t o = (int64_t)i * r + j;
-    C[o] = beta != 0.0 ? acc + beta * Cin[o] : acc;
+  if (i < M && j < N) C[(int64_t)i * ldc + j] = beta != 0.0 ? acc + beta * Cin[(int64_t)i * ldcin + j] : acc;
+}
+
+// dst (r x r, leading dimension ldd) from a dense binary32 r x r matrix
+__global__ void k_to_double_ld(int r, const float* __restrict__ src, double* __restrict__ dst,
+                               int64_t ldd) {
+  const int64_t total = (int64_t)r * r;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = t / r, b = t - a * r;
+    dst[a * ldd + b] = (double)src[t];
   }
 }
 
-__global__ void k_to_double(int64_t count, const float* __restrict__ src, double* __restrict__ dst) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
-       t += (int64_t)gridDim.x * blockDim.x)
-    dst[t] = (double)src[t];
-}
 
 // One Ogita-Aishima update from C = X^T X and S = X^T G X (r x r): lam_i = S_ii / C_ii
 // (= S_ii / (1 - R_ii)), and E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) wherever that
 // first-order correction is small (|E_ij| < 0.1); pairs too close for it to be
 // trustworthy are left as a cluster with E_ij = R_ij / 2, as are the diagonal entries.
-__global__ void k_oa_lambda(int r, const double* __restrict__ C, const double* __restrict__ S,
-                            double* __restrict__ lam) {
+__global__ void k_oa_lambda(int r, const double* __restrict__ CS, double* __restrict__ lam) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < r) lam[i] = S[i * r + i] / C[i * r + i];
+  const int64_t ld = 2 * (int64_t)r;
+  if (i < r) lam[i] = CS[i * ld + r + i] / CS[i * ld + i];
 }
 
-__global__ void k_oa_coeffs(int r, const double* __restrict__ C, const double* __restrict__ S,
-                            const double* __restrict__ lam, double* __restrict__ E) {
+__global__ void k_oa_coeffs(int r, const double* __restrict__ CS, double* __restrict__ E) {
+  const int64_t ld = 2 * (int64_t)r;
   const int rr2 = r * r;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rr2; t += gridDim.x * blockDim.x) {
     const int a = t / r, b = t - (t / r) * r;
-    const double rab = (a == b ? 1.0 : 0.0) - C[t];
+    const double cab = CS[a * ld + b], sab = CS[a * ld + r + b];
+    const double rab = (a == b ? 1.0 : 0.0) - cab;
     double e = 0.5 * rab;
     if (a != b) {
-      const double gap = lam[b] - lam[a];
+      const double la = CS[a * ld + r + a] / CS[a * ld + a];
+      const double lb = CS[b * ld + r + b] / CS[b * ld + b];
+      const double gap = lb - la;
       if (gap != 0.0) {
-        const double f = (S[t] + lam[b] * rab) / gap;
+        const double f = (sab + lb * rab) / gap;
         if (fabs(f) < 0.1) e = f;
       }
     }
@@ -250,9 +257,34 @@ __global__ void k_oa_coeffs(int r, const double* __restrict__ C, const double* _
   }
 }
 
+// Convergence test of the refinement: *status = 1 when an off-diagonal entry of
+// S = X^T G X exceeds tol times its largest diagonal entry (a coupled pair was left
+// unresolved), else 0.
+__global__ void __launch_bounds__(1024)
+k_oa_check(int r, const double* __restrict__ CS, double tol, int* __restrict__ status) {
+  __shared__ double red_off[32], red_diag[32];
+  const int64_t ld = 2 * (int64_t)r;
+  double off = 0.0, dg = 0.0;
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int a = t / r, b = t - (t / r) * r;
+    const double v = fabs(CS[a * ld + r + b]);
+    if (a == b) dg = fmax(dg, v); else off = fmax(off, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
+    dg = fmax(dg, __shfl_xor_sync(0xffffffffu, dg, o));
+  }
+  if ((threadIdx.x & 31) == 0) { red_off[threadIdx.x >> 5] = off; red_diag[threadIdx.x >> 5] = dg; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { off = fmax(off, red_off[w]); dg = fmax(dg, red_diag[w]); }
+    *status = (off <= tol * dg) ? 0 : 1;  // NaN counts as not converged
+  }
+}
+
 // Sort eigenpairs by descending eigenvalue (bitonic over 1024 slots, r <= 1024).
 __global__ void __launch_bounds__(1024)
-k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ X,
+k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ X, int64_t ldx,
            double* __restrict__ lam_out, double* __restrict__ Ub, int64_t ldu) {
   __shared__ double key[1024];
   __shared__ int idx[1024];
@@ -281,83 +313,249 @@ k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ 
   if (t < r) lam_out[t] = key[t];
   // row a of Ub, column j: warp w takes rows w, w + 32, ...; lanes take columns
   for (int a = t >> 5; a < r; a += blockDim.x >> 5)
-    for (int j = t & 31; j < r; j += 32) Ub[(int64_t)a * ldu + j] = X[(int64_t)a * r + idx[j]];
+    for (int j = t & 31; j < r; j += 32) Ub[(int64_t)a * ldu + j] = X[(int64_t)a * ldx + idx[j]];
+}
+
+// Near-diagonal start.  In a recycled basis G = B B^T is close to diagonal: most pairs have
+// a first-order coupling |G_ab| / |G_bb - G_aa| well below one, which the Ogita-Aishima
+// steps resolve directly.  Pairs at or above kClusterTol are joined into clusters
+// (connected components, by label propagation over the list of such pairs); each
+// cluster's block of G is diagonalised by cyclic binary32 Jacobi inside one warp, and
+// X0 is the identity outside the clusters.  *status = 1 (X0 not written) when a cluster
+// has more than kClusterMax members or the pair list overflows: the caller then runs the
+// full Jacobi.
+constexpr double kClusterTol = 0.02;
+constexpr int kClusterMax = 32;
+constexpr int kClusterWarps = 4;
+constexpr int kMaxEdges = 4096;
+
+size_t cluster_smem_bytes() {
+  return sizeof(int) * (3 * 1024 + 2 * kMaxEdges) +
+         sizeof(float) * 2 * kClusterWarps * kClusterMax * (kClusterMax + 1) +
+         sizeof(int) * kClusterWarps * kClusterMax;
+}
+
+__global__ void __launch_bounds__(1024)
+k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __restrict__ X,
+                int64_t ldx, int* __restrict__ status) {
+  extern __shared__ int csm[];
+  int* label = csm;                    // 1024
+  int* cnt = label + 1024;             // 1024
+  int* roots = cnt + 1024;             // 1024
+  int* ea = roots + 1024;              // kMaxEdges
+  int* eb = ea + kMaxEdges;            // kMaxEdges
+  float* blkA = reinterpret_cast<float*>(eb + kMaxEdges);           // warps x 32 x 33
+  float* blkV = blkA + kClusterWarps * kClusterMax * (kClusterMax + 1);
+  int* mem = reinterpret_cast<int*>(blkV + kClusterWarps * kClusterMax * (kClusterMax + 1));
+  __shared__ int nedges, nroots, bad;
+  __shared__ float diag[1024];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < r; i += blockDim.x) {
+    label[i] = i;
+    cnt[i] = 0;
+    diag[i] = (float)G[(int64_t)i * ldg + i];
+  }
+  if (tid == 0) { nedges = 0; nroots = 0; bad = 0; }
+  __syncthreads();
+  // the pair test runs in binary32 (binary64 is a small fraction of the rate): rounding
+  // can only add pairs whose diagonal entries agree to binary32 precision
+  for (int64_t t = tid; t < (int64_t)r * r; t += blockDim.x) {
+    const int a = (int)(t / r), b = (int)(t - (int64_t)a * r);
+    if (a >= b) continue;
+    const float gab = (float)G[(int64_t)a * ldg + b];
+    const float gap = diag[b] - diag[a];
+    if (gab != 0.f && !(fabsf(gab) < (float)kClusterTol * fabsf(gap))) {
+      const int e = atomicAdd(&nedges, 1);
+      if (e < kMaxEdges) { ea[e] = a; eb[e] = b; } else bad = 1;
+    }
+  }
+  __syncthreads();
+  const int ne = nedges < kMaxEdges ? nedges : kMaxEdges;
+  for (int it = 0; it < r && !bad; ++it) {
+    int moved = 0;
+    for (int e = tid; e < ne; e += blockDim.x) {
+      const int la = label[ea[e]], lb = label[eb[e]];
+      if (la != lb) {
+        const int m = la < lb ? la : lb;
+        atomicMin(&label[ea[e]], m);
+        atomicMin(&label[eb[e]], m);
+        moved = 1;
+      }
+    }
+    if (!__syncthreads_or(moved)) break;  // a barrier, and every thread gets the same answer
+  }
+  for (int i = tid; i < r; i += blockDim.x) atomicAdd(&cnt[label[i]], 1);
+  __syncthreads();
+  for (int i = tid; i < r; i += blockDim.x) {
+    if (label[i] == i && cnt[i] >= 2) {
+      if (cnt[i] > kClusterMax) bad = 1;
+      else roots[atomicAdd(&nroots, 1)] = i;
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) *status = 1;
+    return;
+  }
+  for (int64_t t = tid; t < (int64_t)r * r; t += blockDim.x) {
+    const int a = (int)(t / r), b = (int)(t - (int64_t)a * r);
+    X[(int64_t)a * ldx + b] = a == b ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (warp < kClusterWarps) {
+    float* A = blkA + warp * kClusterMax * (kClusterMax + 1);
+    float* V = blkV + warp * kClusterMax * (kClusterMax + 1);
+    int* mb = mem + warp * kClusterMax;
+    constexpr int LD = kClusterMax + 1;
+    for (int c = warp; c < nroots; c += kClusterWarps) {
+      const int root = roots[c];
+      int sz = 0;
+      for (int j0 = 0; j0 < r; j0 += 32) {
+        const bool in = j0 + lane < r && label[j0 + lane] == root;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) mb[sz + __popc(m & ((1u << lane) - 1u))] = j0 + lane;
+        sz += __popc(m);
+      }
+      __syncwarp();
+      for (int a = 0; a < sz; ++a)
+        if (lane < sz) {
+          A[a * LD + lane] = (float)G[(int64_t)mb[a] * ldg + mb[lane]];
+          V[a * LD + lane] = a == lane ? 1.f : 0.f;
+        }
+      __syncwarp();
+      for (int sweep = 0; sweep < 20; ++sweep) {
+        bool any = false;
+        for (int p = 0; p < sz - 1; ++p)
+          for (int q = p + 1; q < sz; ++q) {
+            const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+            const float mag = fabsf(apq);
+            if (!(mag > 1e-6f * fabsf(app - aqq) && mag > 4e-7f * (fabsf(app) + fabsf(aqq))))
+              continue;
+            const float theta = (aqq - app) / (2.f * apq);
+            float t;
+            if (fabsf(theta) > 1e15f) t = 0.5f / theta;
+            else t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+            const float cs = rsqrtf(1.f + t * t), sn = t * cs;
+            __syncwarp();
+            if (lane < sz) {  // rows p, q
+              const float x = A[p * LD + lane], y = A[q * LD + lane];
+              A[p * LD + lane] = cs * x - sn * y;
+              A[q * LD + lane] = sn * x + cs * y;
+            }
+            __syncwarp();
+            if (lane < sz) {  // columns p, q of A and V
+              const float x = A[lane * LD + p], y = A[lane * LD + q];
+              A[lane * LD + p] = cs * x - sn * y;
+              A[lane * LD + q] = sn * x + cs * y;
+              const float u = V[lane * LD + p], v = V[lane * LD + q];
+              V[lane * LD + p] = cs * u - sn * v;
+              V[lane * LD + q] = sn * u + cs * v;
+            }
+            __syncwarp();
+            any = true;
+          }
+        if (!any) break;
+      }
+      for (int a = 0; a < sz; ++a)
+        if (lane < sz) X[(int64_t)mb[a] * ldx + mb[lane]] = (double)V[a * LD + lane];
+      __syncwarp();
+    }
+  }
+  if (tid == 0) *status = 0;
 }
 
 }  // namespace
 
+// Scratch (doubles): binary32 A and V of the Jacobi stage (r^2 doubles of room), then
+// XP = [X | G X] and XPn (r x 2r each), CS = [X^T X | X^T G X] (r x 2r), E (r x r), lam (r).
 size_t eig_scratch(int r) {
-  // floats: A, V (2 r^2) as doubles-equivalent; doubles: X, Xn, C, P, S, E (6 r^2), lam (r)
   const size_t rr = (size_t)r * r;
-  return rr + 6 * rr + (size_t)r + gemm_tn_scratch(r, r, r) + 64;
+  return rr + 7 * rr + (size_t)r + 64;
 }
+
+namespace {
+struct EigWork {
+  float *A32, *V32;
+  double *XP, *XPn, *CS, *E, *lam;
+  EigWork(int r, double* work) {
+    const size_t rr = (size_t)r * r;
+    A32 = reinterpret_cast<float*>(work);
+    V32 = A32 + rr;
+    XP = work + rr;
+    XPn = XP + 2 * rr;
+    CS = XPn + 2 * rr;
+    E = CS + 2 * rr;
+    lam = E + rr;
+  }
+};
+}  // namespace
 
 svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
                      int* sweeps_out) {
   if (r <= 0) return SVT_OK;
   if (r > 1024) return fail(SVT_ERR_UNSUPPORTED, "eigensolver: r = %d exceeds 1024", r);
   const size_t rr = (size_t)r * r;
-  float* A32 = reinterpret_cast<float*>(work);          // r^2 floats
-  float* V32 = A32 + rr;                                // r^2 floats (fits in rr doubles)
-  double* X = work + rr;
-  double* Xn = X + rr;
-  double* C = Xn + rr;
-  double* P = C + rr;
-  double* S = P + rr;
-  double* E = S + rr;
-  double* lamw = E + rr;
-  double* part = lamw + r + 8;
-
+  EigWork w(r, work);
   const size_t smem = 2 * rr * sizeof(float);
   const int use_smem = smem <= 200 * 1024 ? 1 : 0;
   if (use_smem) {
     SVT_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   }
-  k_jacobi32<<<1, kJacThreads, use_smem ? smem : 0, s>>>(r, G, ldg, A32, V32, 12, use_smem,
+  k_jacobi32<<<1, kJacThreads, use_smem ? smem : 0, s>>>(r, G, ldg, w.A32, w.V32, 12, use_smem,
                                                          sweeps_out);
   SVT_LAUNCH_CHECK();
-  k_to_double<<<(int)ceil_div((int64_t)rr, 256), 256, 0, s>>>((int64_t)rr, V32, X);
+  k_to_double_ld<<<(int)ceil_div((int64_t)rr, 256), 256, 0, s>>>(r, w.V32, w.XP, 2 * (int64_t)r);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
+                              int* status) {
+  if (r <= 0 || r > 1024) return fail(SVT_ERR_UNSUPPORTED, "eigensolver: r = %d out of range", r);
+  EigWork w(r, work);
+  const size_t smem = cluster_smem_bytes();
+  SVT_CUDA(cudaFuncSetAttribute(k_cluster_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_cluster_start<<<1, 1024, smem, s>>>(r, G, ldg, w.XP, 2 * (int64_t)r, status);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
 
 svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
-                      double* work, int refine_steps, cudaStream_t s) {
+                      double* work, int refine_steps, cudaStream_t s, int* check_status,
+                      double check_tol) {
   if (r <= 0) return SVT_OK;
-  const size_t rr = (size_t)r * r;
-  double* X = work + rr;
-  double* Xn = X + rr;
-  double* C = Xn + rr;
-  double* P = C + rr;
-  double* S = P + rr;
-  double* E = S + rr;
-  double* lamw = E + rr;
-  double* part = lamw + r + 8;
-  (void)part;
-  const dim3 grid((unsigned)ceil_div(r, kSgTile), (unsigned)ceil_div(r, kSgTile));
-  auto gemm = [&](bool ta, const double* A_, int64_t lda_, const double* B_, double beta,
-                  const double* Cin_, double* C_) -> svt_status {
-    if (ta) k_small_gemm<true><<<grid, kSgTile * kSgTile, 0, s>>>(r, A_, lda_, B_, beta, Cin_, C_);
-    else k_small_gemm<false><<<grid, kSgTile * kSgTile, 0, s>>>(r, A_, lda_, B_, beta, Cin_, C_);
+  EigWork w(r, work);
+  const int64_t l2 = 2 * (int64_t)r;
+  auto gemm = [&](bool ta, int M, int N, int K, const double* A_, int64_t lda_, const double* B_,
+                  int64_t ldb_, double beta, const double* Cin_, int64_t ldcin_, double* C_,
+                  int64_t ldc_) -> svt_status {
+    const dim3 grid((unsigned)ceil_div(N, kSgTile), (unsigned)ceil_div(M, kSgTile));
+    if (ta) k_small_gemm<true><<<grid, kSgTile * kSgTile, 0, s>>>(M, N, K, A_, lda_, B_, ldb_, beta, Cin_, ldcin_, C_, ldc_);
+    else k_small_gemm<false><<<grid, kSgTile * kSgTile, 0, s>>>(M, N, K, A_, lda_, B_, ldb_, beta, Cin_, ldcin_, C_, ldc_);
     SVT_LAUNCH_CHECK();
     return SVT_OK;
   };
   const int steps = refine_steps > 0 ? refine_steps : 0;
   const int eb = (int)ceil_div((int64_t)r * r, 256);
+  double* XP = w.XP;
+  double* XPn = w.XPn;
   for (int step = 0; step <= steps; ++step) {
-    SVT_TRY(gemm(true, X, r, X, 0.0, nullptr, C));     // X^T X
-    SVT_TRY(gemm(false, G, ldg, X, 0.0, nullptr, P));  // G X
-    SVT_TRY(gemm(true, X, r, P, 0.0, nullptr, S));     // X^T G X
-    k_oa_lambda<<<(int)ceil_div(r, 256), 256, 0, s>>>(r, C, S, lamw);
+    SVT_TRY(gemm(false, r, r, r, G, ldg, XP, l2, 0.0, nullptr, 0, XP + r, l2));    // P = G X
+    SVT_TRY(gemm(true, r, 2 * r, r, XP, l2, XP, l2, 0.0, nullptr, 0, w.CS, l2));  // X^T [X | P]
+    if (step == steps) break;                                                     // eigenvalues only
+    k_oa_coeffs<<<eb < 1024 ? eb : 1024, 256, 0, s>>>(r, w.CS, w.E);
     SVT_LAUNCH_CHECK();
-    if (step == steps) break;                           // last pass: eigenvalues only
-    k_oa_coeffs<<<eb < 1024 ? eb : 1024, 256, 0, s>>>(r, C, S, lamw, E);
-    SVT_LAUNCH_CHECK();
-    SVT_TRY(gemm(false, X, r, E, 1.0, X, Xn));          // X + X E
-    double* t = X; X = Xn; Xn = t;
+    SVT_TRY(gemm(false, r, r, r, XP, l2, w.E, r, 1.0, XP, l2, XPn, l2));           // X + X E
+    double* t = XP; XP = XPn; XPn = t;
   }
-  k_sort_eig<<<1, 1024, 0, s>>>(r, lamw, X, lam, Ub, ldu);
+  k_oa_lambda<<<(int)ceil_div(r, 256), 256, 0, s>>>(r, w.CS, w.lam);
+  SVT_LAUNCH_CHECK();
+  if (check_status) {
+    k_oa_check<<<1, 1024, 0, s>>>(r, w.CS, check_tol, check_status);
+    SVT_LAUNCH_CHECK();
+  }
+  k_sort_eig<<<1, 1024, 0, s>>>(r, w.lam, XP, l2, lam, Ub, ldu);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }

@@ -71,8 +71,13 @@ svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub,
 // binary64 refinement and the sort.
 svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
                      int* sweeps_out);
+// Near-diagonal start for eig_refine (recycled bases): *status (device int) = 0 when the
+// start was written, 1 when a coupled cluster is too large (run eig_start instead).
+svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
+                              int* status);
 svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
-                      double* work, int refine_steps, cudaStream_t s);
+                      double* work, int refine_steps, cudaStream_t s, int* check_status = nullptr,
+                      double check_tol = 0.0);
 
 // update.cu -------------------------------------------------------------------
 size_t reduce_scratch();

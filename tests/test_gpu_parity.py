@@ -207,6 +207,55 @@ def test_r4svd_parity(svt, torch_mod, eps_thr, n_power):
     assert _rel(Xg, Xo) < FP64_TOL
 
 
+def _oracle_state(w, it_stop, **kw):
+    """(Y in CSR order at SVT iteration it_stop, the basis that iteration recycles), from
+    the oracle's own solve."""
+    captured = {}
+    orig = OF.r4svd
+
+    def spy(Ys, U_prev, eps_thr, it, **kws):
+        if it == it_stop:
+            captured["y"] = Ys
+            captured["U_prev"] = None if U_prev is None else np.array(U_prev)
+            captured["eps_thr"] = eps_thr
+        return orig(Ys, U_prev, eps_thr, it, **kws)
+    OF.r4svd = spy
+    try:
+        OF.svt(w.m, w.n, w.rows, w.cols, w.vals, w.tau, w.delta, 0.0, it_stop, seed=w.seed, **kw)
+    finally:
+        OF.r4svd = orig
+    return captured
+
+
+@pytest.mark.parametrize("name,it_stop,kw", [
+    ("recovery40", 206, dict(eps_thr0=1e-12)),
+    ("recovery40", 8, dict(eps_thr0=1e-12)),
+    ("lowrank500", 30, dict()),
+])
+def test_r4svd_recycled_near_diagonal(svt, torch_mod, name, it_stop, kw):
+    """Recycled calls start the binary64 refinement from the near-diagonal Gram matrix
+    (coupled clusters diagonalised); every singular value must still match the oracle.
+    At iteration 8 of the 40 x 40 recovery, clusters of 23, 10 and 3 leave a coupled pair
+    unresolved, and the result must come from the Jacobi fallback."""
+    if name == "recovery40":
+        w = workloads.random_lowrank(40, 40, 2, 0.6, seed=33, tol=1e-9, maxit=1000)
+    else:
+        w = workloads.small_lowrank()
+    st = _oracle_state(w, it_stop, **kw)
+    ref_p = oracle.build_pattern(w.m, w.n, w.rows, w.cols)
+    Ys = st["y"].tocsr()
+    y = np.asarray(Ys[ref_p.csr_rows(), ref_p.col_idx]).ravel()
+    P = svt.Pattern(w.m, w.n, w.rows, w.cols)
+    U_prev = st["U_prev"]
+    ro = oracle.r4svd(Ys, U_prev, st["eps_thr"], it_stop, r_cap=min(w.m, w.n), seed=w.seed, t=1,
+                      dt=10, n_power=0)
+    rg = svt.r4svd(P, torch_mod.from_numpy(y), st["eps_thr"], it_stop, U_prev=torch_mod.from_numpy(U_prev),
+                   seed=w.seed, dt=10)
+    assert (rg["r"], rg["blocks"]) == (ro.r, ro.blocks)
+    S = rg["S"].cpu().numpy()
+    assert np.max(np.abs(S - ro.S)) / ro.S[0] < FP64_TOL, (S[:4], ro.S[:4])
+
+
 def test_r4svd_exhausted_range(svt, torch_mod):
     """A rank-3 matrix with a full pattern and a threshold no error percentage can meet:
     the block after the first finds the range exhausted and is discarded."""
