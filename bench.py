@@ -327,6 +327,8 @@ def our_arm(args):
     # roofline of the dominant kernel class
     peaks, peak_src = load_peaks()
     sweeps = prof.pop("jacobi_sweeps", None)
+    events = {k: prof.pop(k)["launches"] for k in ("eig_start_oversize", "eig_start_rejected",
+                                                   "eig_start_rejected_twice") if k in prof}
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
     roofline = None
     if dom:
@@ -379,6 +381,7 @@ def our_arm(args):
             "roofline": roofline,
             "kernels": breakdown,
             "jacobi_sweeps_per_call": (sweeps["bytes"] / max(sweeps["launches"], 1)) if sweeps else None,
+            "eig_start_events": events,
             "cpu_baseline": cpu,
             "clocks": clock_info,
         }

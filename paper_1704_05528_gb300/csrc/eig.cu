@@ -58,24 +58,16 @@ __device__ __forceinline__ bool jac_active(float app, float aqq, float apq, floa
 // anything (the matrix is unchanged by a sweep without rotations, so this is the same
 // test as running that sweep).  With N = r rounded up to even, a pair whose partner is
 // the padding index r rotates nothing and has a single row / column.
-__global__ void __launch_bounds__(kJacThreads)
-k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* gV,
-           int max_sweeps, int use_smem, int* sweeps_out) {
-  extern __shared__ float dyn[];
+// Cyclic Jacobi sweeps on an r x r binary32 matrix A (row-major, shared or global memory)
+// accumulating the rotations into V; every thread of the (kJacThreads) block takes part.
+// Returns the number of sweeps that rotated.
+__device__ int jacobi_sweeps(int r, float* A, float* V, int max_sweeps) {
   __shared__ float cs_c[kJacThreads / 2 + 1], cs_s[kJacThreads / 2 + 1];
   __shared__ int pp[kJacThreads / 2 + 1], qq[kJacThreads / 2 + 1];
   __shared__ int active_any, check_any;
   __shared__ int step_flag[3];
   __shared__ float scale;
-  float* A = use_smem ? dyn : gA;
-  float* V = use_smem ? dyn + r * r : gV;
   const int tid = threadIdx.x;
-  for (int a = tid / 32; a < r; a += kJacThreads / 32)
-    for (int b = tid % 32; b < r; b += 32) {
-      A[a * r + b] = (float)G[(int64_t)a * ldg + b];
-      V[a * r + b] = (a == b) ? 1.0f : 0.0f;
-    }
-  __syncthreads();
   if (tid < 32) {
     float mx = 0.f;
     for (int i = tid; i < r; i += 32) mx = fmaxf(mx, fabsf(A[i * r + i]));
@@ -174,6 +166,24 @@ k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* g
     if (tid == 0) active_any = 0;
     __syncthreads();
   }
+  __syncthreads();
+  return sweep;
+}
+
+__global__ void __launch_bounds__(kJacThreads)
+k_jacobi32(int r, const double* __restrict__ G, int64_t ldg, float* gA, float* gV,
+           int max_sweeps, int use_smem, int* sweeps_out) {
+  extern __shared__ float dyn[];
+  float* A = use_smem ? dyn : gA;
+  float* V = use_smem ? dyn + r * r : gV;
+  const int tid = threadIdx.x;
+  for (int a = tid / 32; a < r; a += kJacThreads / 32)
+    for (int b = tid % 32; b < r; b += 32) {
+      A[a * r + b] = (float)G[(int64_t)a * ldg + b];
+      V[a * r + b] = (a == b) ? 1.0f : 0.0f;
+    }
+  __syncthreads();
+  const int sweep = jacobi_sweeps(r, A, V, max_sweeps);
   if (use_smem) {
     for (int t = tid; t < r * r; t += blockDim.x) gV[t] = V[t];
   }
@@ -322,22 +332,26 @@ k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ 
 // (connected components, by label propagation over the list of such pairs); each
 // cluster's block of G is diagonalised by cyclic binary32 Jacobi inside one warp, and
 // X0 is the identity outside the clusters.  *status = 1 (X0 not written) when a cluster
-// has more than kClusterMax members or the pair list overflows: the caller then runs the
-// full Jacobi.
+// has more than kBigClusterMax members or the pair list overflows: the caller then runs
+// the full Jacobi.  Clusters of up to kClusterMax members are solved one per warp; larger
+// ones (up to kBigClusterMax) one at a time by the whole block with the cyclic Jacobi of
+// k_jacobi32 on the cluster's block.
 constexpr double kClusterTol = 0.02;
 constexpr int kClusterMax = 32;
+constexpr int kBigClusterMax = 96;
 constexpr int kClusterWarps = 4;
 constexpr int kMaxEdges = 4096;
 
 size_t cluster_smem_bytes() {
   return sizeof(int) * (3 * 1024 + 2 * kMaxEdges) +
          sizeof(float) * 2 * kClusterWarps * kClusterMax * (kClusterMax + 1) +
-         sizeof(int) * kClusterWarps * kClusterMax;
+         sizeof(int) * kClusterWarps * kClusterMax +
+         sizeof(float) * 2 * kBigClusterMax * kBigClusterMax + sizeof(int) * kBigClusterMax;
 }
 
 __global__ void __launch_bounds__(1024)
 k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __restrict__ X,
-                int64_t ldx, int* __restrict__ status) {
+                int64_t ldx, int* __restrict__ status, int identity_on_fail) {
   extern __shared__ int csm[];
   int* label = csm;                    // 1024
   int* cnt = label + 1024;             // 1024
@@ -347,7 +361,10 @@ k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __rest
   float* blkA = reinterpret_cast<float*>(eb + kMaxEdges);           // warps x 32 x 33
   float* blkV = blkA + kClusterWarps * kClusterMax * (kClusterMax + 1);
   int* mem = reinterpret_cast<int*>(blkV + kClusterWarps * kClusterMax * (kClusterMax + 1));
-  __shared__ int nedges, nroots, bad;
+  float* bigA = reinterpret_cast<float*>(mem + kClusterWarps * kClusterMax);  // big cluster
+  float* bigV = bigA + kBigClusterMax * kBigClusterMax;
+  int* bigm = reinterpret_cast<int*>(bigV + kBigClusterMax * kBigClusterMax);
+  __shared__ int nedges, nroots, bad, bigsz;
   __shared__ float diag[1024];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < r; i += blockDim.x) {
@@ -388,18 +405,18 @@ k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __rest
   __syncthreads();
   for (int i = tid; i < r; i += blockDim.x) {
     if (label[i] == i && cnt[i] >= 2) {
-      if (cnt[i] > kClusterMax) bad = 1;
-      else roots[atomicAdd(&nroots, 1)] = i;
+      if (cnt[i] > kBigClusterMax) bad = 1;
+      else if (cnt[i] <= kClusterMax) roots[atomicAdd(&nroots, 1)] = i;
     }
   }
   __syncthreads();
+  for (int64_t t = tid; t < (int64_t)r * r && (!bad || identity_on_fail); t += blockDim.x) {
+    const int a = (int)(t / r), b = (int)(t - (int64_t)a * r);
+    X[(int64_t)a * ldx + b] = a == b ? 1.0 : 0.0;
+  }
   if (bad) {
     if (tid == 0) *status = 1;
     return;
-  }
-  for (int64_t t = tid; t < (int64_t)r * r; t += blockDim.x) {
-    const int a = (int)(t / r), b = (int)(t - (int64_t)a * r);
-    X[(int64_t)a * ldx + b] = a == b ? 1.0 : 0.0;
   }
   __syncthreads();
   if (warp < kClusterWarps) {
@@ -461,6 +478,35 @@ k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __rest
       __syncwarp();
     }
   }
+  __syncthreads();
+  // clusters above kClusterMax, one at a time, by the whole block (roots in index order)
+  for (int root = 0; root < r; ++root) {
+    if (!(label[root] == root && cnt[root] > kClusterMax)) continue;  // uniform: shared data
+    if (warp == 0) {  // members in index order
+      int sz = 0;
+      for (int j0 = 0; j0 < r; j0 += 32) {
+        const bool in = j0 + lane < r && label[j0 + lane] == root;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) bigm[sz + __popc(m & ((1u << lane) - 1u))] = j0 + lane;
+        sz += __popc(m);
+      }
+      if (lane == 0) bigsz = sz;
+    }
+    __syncthreads();
+    const int sz = bigsz;
+    for (int t = tid; t < sz * sz; t += blockDim.x) {
+      const int a = t / sz, b = t - (t / sz) * sz;
+      bigA[t] = (float)G[(int64_t)bigm[a] * ldg + bigm[b]];
+      bigV[t] = a == b ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_sweeps(sz, bigA, bigV, 12);
+    for (int t = tid; t < sz * sz; t += blockDim.x) {
+      const int a = t / sz, b = t - (t / sz) * sz;
+      X[(int64_t)bigm[a] * ldx + bigm[b]] = (double)bigV[t];
+    }
+    __syncthreads();
+  }
   if (tid == 0) *status = 0;
 }
 
@@ -516,9 +562,30 @@ svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work,
   EigWork w(r, work);
   const size_t smem = cluster_smem_bytes();
   SVT_CUDA(cudaFuncSetAttribute(k_cluster_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_cluster_start<<<1, 1024, smem, s>>>(r, G, ldg, w.XP, 2 * (int64_t)r, status);
+  k_cluster_start<<<1, 1024, smem, s>>>(r, G, ldg, w.XP, 2 * (int64_t)r, status, 0);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
+}
+
+svt_status eig_refine_clusters_again(int r, const double* G, int64_t ldg, double* lam, double* Ub,
+                                     int64_t ldu, double* work, int refine_steps, cudaStream_t s,
+                                     int* status, double tol) {
+  EigWork w(r, work);
+  const int64_t l2 = 2 * (int64_t)r;
+  // clusters of the pairs that S = X^T G X still couples, diagonalised into X1 (identity
+  // if a cluster is too large: the check below then fails again)
+  const size_t smem = cluster_smem_bytes();
+  SVT_CUDA(cudaFuncSetAttribute(k_cluster_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_cluster_start<<<1, 1024, smem, s>>>(r, w.CS + r, l2, w.E, r, status, 1);
+  SVT_LAUNCH_CHECK();
+  // X <- X X1
+  const dim3 grid((unsigned)ceil_div(r, kSgTile), (unsigned)ceil_div(r, kSgTile));
+  k_small_gemm<false><<<grid, kSgTile * kSgTile, 0, s>>>(r, r, r, w.XP, l2, w.E, r, 0.0, nullptr, 0,
+                                                          w.XPn, l2);
+  SVT_LAUNCH_CHECK();
+  SVT_CUDA(cudaMemcpy2DAsync(w.XP, l2 * sizeof(double), w.XPn, l2 * sizeof(double),
+                             (size_t)r * sizeof(double), r, cudaMemcpyDeviceToDevice, s));
+  return eig_refine(r, G, ldg, lam, Ub, ldu, work, refine_steps, s, status, tol);
 }
 
 svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,

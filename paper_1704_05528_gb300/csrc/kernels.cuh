@@ -75,6 +75,11 @@ svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStre
 // start was written, 1 when a coupled cluster is too large (run eig_start instead).
 svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
                               int* status);
+// After a rejected eig_refine from that start: diagonalise the clusters of pairs that
+// X^T G X still couples, rotate X, refine again with the same acceptance test.
+svt_status eig_refine_clusters_again(int r, const double* G, int64_t ldg, double* lam, double* Ub,
+                                     int64_t ldu, double* work, int refine_steps, cudaStream_t s,
+                                     int* status, double tol);
 svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
                       double* work, int refine_steps, cudaStream_t s, int* check_status = nullptr,
                       double check_tol = 0.0);

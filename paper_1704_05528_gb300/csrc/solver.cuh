@@ -85,6 +85,13 @@ inline void prof_flush() {
   cudaGetLastError();
 }
 
+// Count an event (no timing) in the table, when profiling is on.
+inline void prof_count(const char* name) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof[prof_id(name)].launches += 1;
+}
+
 struct ProfScope {
   bool on;
   int id = -1;
@@ -392,6 +399,7 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     }
     SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaStreamSynchronize(st));
+    if (status != 0) prof_count("eig_start_oversize");
     if (status == 0) {
       {
         SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
@@ -400,7 +408,17 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
       }
       SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
       SVT_CUDA(cudaStreamSynchronize(st));
-      near_diagonal = status == 0;  // else an unresolved pair: redo from the full Jacobi
+      if (status != 0) {  // an unresolved pair: resolve its cluster in the rotated basis, once
+        prof_count("eig_start_rejected");
+        SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+        SVT_TRY(eig_refine_clusters_again(r, W.G, r, W.lam, W.Ub, r, W.eigw, 2, st,
+                                          reinterpret_cast<int*>(W.flags + 3),
+                                          near_diagonal_tol<T>()));
+        SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SVT_CUDA(cudaStreamSynchronize(st));
+        if (status != 0) prof_count("eig_start_rejected_twice");
+      }
+      near_diagonal = status == 0;  // else redo from the full Jacobi
     }
   }
   if (!near_diagonal) {
