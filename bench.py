@@ -174,7 +174,9 @@ def oracle_sample(name, iters):
                      r_max=w.r_max, seed=w.seed)
     wall = time.perf_counter() - t0
     it_s = [e["seconds"] for e in res.log]
-    print(json.dumps({"iters": len(it_s), "iter_seconds": it_s, "wall": wall}))
+    meta = {"workload": w.name, "m": w.m, "n": w.n, "nnz_train": w.nnz, "r_max": w.r_max,
+            "tau": w.tau, "delta": w.delta, "tol": w.tol, "maxit": w.maxit}
+    print(json.dumps({"iters": len(it_s), "iter_seconds": it_s, "wall": wall, "meta": meta}))
 
 
 def run_oracle_child(name, iters, threads, timeout=600):
@@ -210,7 +212,9 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "precision": "fp64 (CPU oracle)"},
+        "data": "synthetic",
+        "config": dict(d["meta"], precision="fp64 (CPU oracle)", parallelism="replicas x1",
+                       l2="n/a (host cores)", iters_per_step=1.0),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
