@@ -33,8 +33,9 @@ if ROOT not in sys.path:
 
 METRIC = "SVT iterations/s (fast SVT with R4SVD)"
 UNIT = "iter/s"
-HBM_KERNELS = {"spmm_csr", "spmm_csc", "spmm_csc_recycled", "sampled_update", "gather_csc",
-               "init_power", "lift_U", "lift_V", "gram_B", "orthogonalise", "cholqr"}
+HBM_KERNELS = {"spmm_csr", "spmm_csc", "spmm_csc_recycled", "sampled_update", "update_recycled",
+               "gather_csc", "scatter_csr", "init_power", "lift_U", "lift_V", "gram_B",
+               "orthogonalise", "cholqr"}
 
 
 def parse_args():
@@ -332,7 +333,8 @@ def our_arm(args):
     peaks, peak_src = load_peaks()
     sweeps = prof.pop("jacobi_sweeps", None)
     events = {k: prof.pop(k)["launches"] for k in ("eig_start_oversize", "eig_start_rejected",
-                                                   "eig_start_rejected_twice") if k in prof}
+                                                   "eig_start_rejected_twice",
+                                                   "eig_graph_unavailable") if k in prof}
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
     roofline = None
     if dom:

@@ -171,6 +171,25 @@ svt_status svt_sampled_update(const svt_pattern* p, int precision, const void* U
                               const void* a_csr, void* y_csr, double delta, double* sums,
                               void* stream);
 
+/* The same pass in CSC order fused with the next iteration's recycled product: R4SVD
+ * with recycling (Algorithm 3) starts from the basis U that defines X^(i), so
+ * B^T = (Y^(i+1))^T U can be formed while the update gathers U's rows.  For each observed
+ * (p, q) in CSC order: x = sum_{j<k} U[p, j] * W[q, j], d = a - x, y += delta * d; then
+ * Bt[q, :r] = sum over column q of y_new * U[p, :r].
+ *   U      m x r basis (ldu), device, 16-byte aligned, ldu a multiple of 4 (binary32) or
+ *          2 (binary64) elements and at least r rounded up to that multiple;
+ *   W      n x k (ldw), device, same alignment rule for k;
+ *   a_csc, y_csc  observed values and Y in the pattern's CSC order (device, nnz each);
+ *          y_csc is updated in place;
+ *   Bt     n x r (ldb >= r), device, overwritten (rows of empty columns are zero);
+ *   sums   host, as in svt_sampled_update.
+ * 1 <= r <= 512 (binary32) or 256 (binary64) and 0 <= k <= r, else SVT_ERR_ARG;
+ * misaligned U or W gives SVT_ERR_UNSUPPORTED.  Bt does not depend on scheduling. */
+svt_status svt_sampled_update_recycle(const svt_pattern* p, int precision, const void* U,
+                                      int64_t ldu, int32_t r, const void* W, int64_t ldw,
+                                      int32_t k, const void* a_csc, void* y_csc, double delta,
+                                      void* Bt, int64_t ldb, double* sums, void* stream);
+
 /* ------------------------------------------------------------------ R4SVD */
 /* One call of R4SVD (Algorithm 3; Algorithm 2 when s == 0) on Y given in CSR order
  * on the pattern.  U_prev: m x s recycled left singular vectors (ld_prev), may be NULL

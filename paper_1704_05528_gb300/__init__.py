@@ -15,6 +15,7 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "spmm_noalloc", "sampled_update",
+           "sampled_update_recycle",
            "r4svd", "complete", "library", "launch_count", "profile_enable", "profile_reset", "profile_read",
            "unrolled_grad", "unrolled_params", "SVTUnrolled", "FP64", "MIXED_FP32"]
 
@@ -184,6 +185,32 @@ def sampled_update(pattern: Pattern, U, W, a_csr, y_csr, delta, precision="fp64"
     _check(library().svt_sampled_update(pattern.handle, prec, _ptr(U), max(k, 1), _ptr(W), max(k, 1), k,
                                         _ptr(a), _ptr(y_csr), float(delta), sums, _stream_ptr()))
     return tuple(sums)
+
+
+def sampled_update_recycle(pattern: Pattern, U, W, a_csc, y_csc, delta, precision="fp64"):
+    """In place on y_csc (CSC order): y += delta (a - (U[:, :k] W^T) on Lambda), with k the
+    width of W; returns (Bt, sums) with Bt (n x r) = y_new^T U and sums as in
+    sampled_update."""
+    torch = _torch()
+    prec = _prec(precision)
+    dt = _vdtype(prec)
+    vec = 2 if dt == torch.float64 else 4
+    m, r = U.shape
+    k = W.shape[1]
+    n = W.shape[0]
+    ldu, ldw = -(-r // vec) * vec, max(-(-k // vec) * vec, vec)
+    Up = torch.zeros((m, ldu), device="cuda", dtype=dt)
+    Up[:, :r] = U.to(device="cuda", dtype=dt)
+    Wp = torch.zeros((n, ldw), device="cuda", dtype=dt)
+    Wp[:, :k] = W.to(device="cuda", dtype=dt)
+    a = a_csc.to(device="cuda", dtype=dt).contiguous()
+    assert y_csc.is_cuda and y_csc.dtype == dt and y_csc.is_contiguous()
+    Bt = torch.empty((n, r), device="cuda", dtype=dt)
+    sums = (C.c_double * 3)()
+    _check(library().svt_sampled_update_recycle(pattern.handle, prec, _ptr(Up), ldu, r, _ptr(Wp), ldw,
+                                                k, _ptr(a), _ptr(y_csc), float(delta), _ptr(Bt), r,
+                                                sums, _stream_ptr()))
+    return Bt, tuple(sums)
 
 
 def r4svd(pattern: Pattern, y_csr, eps_thr, it, U_prev=None, precision="fp64", **kw):

@@ -67,6 +67,8 @@ SIGNATURES = {
     "svt_spmm": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _I64, _I32, _P, _I64, _P]),
     "svt_spmm_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _I64, _I32, _P, _I64, _P]),
     "svt_sampled_update": (C.c_int, [_P, C.c_int, _P, _I64, _P, _I64, _I32, _P, _P, _D, _PD, _P]),
+    "svt_sampled_update_recycle": (C.c_int, [_P, C.c_int, _P, _I64, _I32, _P, _I64, _I32, _P, _P,
+                                             _D, _P, _I64, _PD, _P]),
     "svt_r4svd": (C.c_int, [_P, _P, _P, _I64, _I32, _D, _U32, C.POINTER(Options), _P, _I64, _P,
                             _P, _I64, _PI32, _PD, _PI32]),
     "svt_profile_enable": (None, [C.c_int]),

@@ -23,6 +23,10 @@ svt_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
 
 // Every kernel launch site is followed by this check; it also counts the launch.
 void count_launch();
+// Adjusts the launch counter (a captured graph's kernels are counted at each launch of
+// the graph, not when they are recorded).
+void count_launches(int64_t delta);
+int64_t launches_so_far();
 #define SVT_LAUNCH_CHECK()        \
   do {                            \
     ::svt::count_launch();        \

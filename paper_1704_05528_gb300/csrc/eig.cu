@@ -18,6 +18,7 @@
 // The eigenpairs are finally sorted by descending eigenvalue.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "common.cuh"
@@ -556,13 +557,29 @@ svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStre
   return SVT_OK;
 }
 
+// The cluster kernel's shared-memory limit is raised once per device: the call is not a
+// stream operation, so it must stay out of graph captures.
+static std::atomic<uint64_t> g_cluster_attr_devices{0};
+
+svt_status eig_prepare() {
+  int dev = 0;
+  SVT_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (g_cluster_attr_devices.load() & bit) return SVT_OK;
+  SVT_CUDA(cudaFuncSetAttribute(k_cluster_start, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cluster_smem_bytes()));
+  g_cluster_attr_devices.fetch_or(bit);
+  return SVT_OK;
+}
+
 svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
-                              int* status) {
+                              int* status, bool identity_on_fail) {
   if (r <= 0 || r > 1024) return fail(SVT_ERR_UNSUPPORTED, "eigensolver: r = %d out of range", r);
   EigWork w(r, work);
   const size_t smem = cluster_smem_bytes();
-  SVT_CUDA(cudaFuncSetAttribute(k_cluster_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_cluster_start<<<1, 1024, smem, s>>>(r, G, ldg, w.XP, 2 * (int64_t)r, status, 0);
+  SVT_TRY(eig_prepare());
+  k_cluster_start<<<1, 1024, smem, s>>>(r, G, ldg, w.XP, 2 * (int64_t)r, status,
+                                        identity_on_fail ? 1 : 0);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -575,7 +592,7 @@ svt_status eig_refine_clusters_again(int r, const double* G, int64_t ldg, double
   // clusters of the pairs that S = X^T G X still couples, diagonalised into X1 (identity
   // if a cluster is too large: the check below then fails again)
   const size_t smem = cluster_smem_bytes();
-  SVT_CUDA(cudaFuncSetAttribute(k_cluster_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SVT_TRY(eig_prepare());
   k_cluster_start<<<1, 1024, smem, s>>>(r, w.CS + r, l2, w.E, r, status, 1);
   SVT_LAUNCH_CHECK();
   // X <- X X1

@@ -33,6 +33,20 @@ svt_status launch_spmm_rows(int64_t nrows, const int32_t* ptr, const int32_t* id
 template <typename T>
 svt_status launch_gather(int64_t count, const int32_t* perm, const T* src, T* dst,
                          cudaStream_t s);
+// dst[perm[q]] = src[q] (the inverse of launch_gather for a permutation)
+template <typename T>
+svt_status launch_scatter(int64_t count, const int32_t* perm, const T* src, T* dst,
+                          cudaStream_t s);
+// Where a kernel that follows the chunking of launch_spmm_rows (chunk_size(nnz) entries
+// per warp) leaves the partial rows of rows that cross chunks: per chunk c, the head slot
+// part[2c * ldp] (its first row) and the tail slot part[(2c + 1) * ldp] (its last row),
+// and tails[c] = the row left in the tail slot, or -1.
+template <typename TD>
+void spmm_slots(void* scratch, int64_t nnz, int w, TD** part, int64_t* ldp, int32_t** tails);
+// out[tails[c]] = tail(c) + head(c + 1) + ... for every chunk c with a tail, in chunk order
+template <typename TD>
+svt_status spmm_fixup(int64_t nnz, const int32_t* ptr, const TD* part, int64_t ldp,
+                      const int32_t* tails, int w, TD* out, int64_t ldo, cudaStream_t s);
 
 // dense.cu --------------------------------------------------------------------
 // C (p x q, binary64, ldc) = A^T B with A (M x p), B (M x q), reduction over M split
@@ -72,9 +86,13 @@ svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub,
 svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
                      int* sweeps_out);
 // Near-diagonal start for eig_refine (recycled bases): *status (device int) = 0 when the
-// start was written, 1 when a coupled cluster is too large (run eig_start instead).
+// start was written, 1 when a coupled cluster is too large (run eig_start instead; with
+// identity_on_fail the start is then the identity, so a refinement can follow unchecked).
 svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
-                              int* status);
+                              int* status, bool identity_on_fail = false);
+// Per-device set-up of the eigensolver kernels (shared-memory limits); call it before a
+// stream capture that records eig_start_clusters.
+svt_status eig_prepare();
 // After a rejected eig_refine from that start: diagonalise the clusters of pairs that
 // X^T G X still couples, rotate X, refine again with the same acceptance test.
 svt_status eig_refine_clusters_again(int r, const double* G, int64_t ldg, double* lam, double* Ub,
@@ -103,5 +121,20 @@ template <typename T>
 svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T* W,
                           int64_t ldw, int k, const T* a, T* y, double delta, double* out3,
                           double* part, unsigned* flags, cudaStream_t s, bool w_pad_zero = false);
+// The sampled update in CSC order fused with the next recycled product: Y (CSC order,
+// a the observed values in CSC order) += delta (A - U[:, :k] W^T) on Lambda, out3 as
+// above, and bt (n x r, ldb) = Y_new^T U[:, :r].  Needs U, W 16-byte aligned with leading
+// dimensions of whole vectors covering r columns, r and nnz within update_recycle_fits,
+// k <= r,
+// `part` of update_recycle_scratch(nnz) doubles and `scratch` of
+// spmm_scratch_bytes(nnz, r, sizeof(T)) bytes.
+template <typename T>
+bool update_recycle_fits(int r, int64_t nnz);
+size_t update_recycle_scratch(int64_t nnz);
+template <typename T>
+svt_status update_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, const T* W,
+                          int64_t ldw, int k, const T* a, T* y, double delta, T* bt, int64_t ldb,
+                          double* out3, double* part, unsigned* flags, void* scratch,
+                          cudaStream_t s);
 
 }  // namespace svt

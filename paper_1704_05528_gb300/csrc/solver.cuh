@@ -36,7 +36,12 @@ struct Pending {
   int id;
   cudaEvent_t a, b;
   double bytes;
+  bool owned = false;  // events belong to a captured graph: not returned to the pool
 };
+// While a stream capture is being recorded on this thread, profiler scopes record their
+// events as nodes of the graph (external event records) into this list instead of the
+// pending list; every launch of the graph then re-queues them.
+extern thread_local std::vector<Pending>* g_prof_capture;
 extern std::mutex g_prof_mu;
 extern bool g_prof_on;
 extern std::vector<ProfEntry> g_prof;
@@ -75,8 +80,10 @@ inline void prof_flush() {
       g_prof[p.id].launches += 1;
       g_prof[p.id].ms += ms;
       g_prof[p.id].bytes += p.bytes;
-      g_pool.push_back(p.a);
-      g_pool.push_back(p.b);
+      if (!p.owned) {
+        g_pool.push_back(p.a);
+        g_pool.push_back(p.b);
+      }
     } else {
       g_pending[keep++] = p;
     }
@@ -102,15 +109,27 @@ struct ProfScope {
     if (!on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     id = prof_id(name);
-    a = pool_event();
-    cudaEventRecord(a, s);
+    if (g_prof_capture) {
+      cudaEventCreate(&a);
+      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+    } else {
+      a = pool_event();
+      cudaEventRecord(a, s);
+    }
   }
   ~ProfScope() {
     if (!on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    cudaEvent_t b = pool_event();
-    cudaEventRecord(b, s);
-    g_pending.push_back(Pending{id, a, b, bytes});
+    cudaEvent_t b = nullptr;
+    if (g_prof_capture) {
+      cudaEventCreate(&b);
+      cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+      g_prof_capture->push_back(Pending{id, a, b, bytes, true});
+    } else {
+      b = pool_event();
+      cudaEventRecord(b, s);
+      g_pending.push_back(Pending{id, a, b, bytes});
+    }
   }
 };
 
@@ -124,6 +143,11 @@ inline double spmm_bytes(int64_t nnz, int64_t rows, int64_t cols, int w, int sv)
 }
 inline double update_bytes(int64_t nnz, int64_t m, int64_t n, int k, int sv) {
   return (double)nnz * (4 + 3 * sv) + 4.0 * (m + 1) + (double)sv * k * (double)(m + n);
+}
+// the fused update: indices, A, Y read and written, U[:, :r] and W[:, :k] once, B^T written
+inline double recycle_bytes(int64_t nnz, int64_t m, int64_t n, int k, int r, int sv) {
+  return (double)nnz * (4 + 3 * sv) + 4.0 * (n + 1) +
+         (double)sv * ((double)m * r + (double)n * k + (double)n * r);
 }
 inline double gemm_bytes(int64_t M, int p, int q, int sv, bool reads_c) {
   return (double)sv * (double)M * (p + q + (reads_c ? q : 0));
@@ -199,6 +223,29 @@ __global__ void k_normalize(int64_t n, const double* __restrict__ w, const doubl
 }  // namespace
 
 // Device buffers of one solve (or one R4SVD call).
+// An executable graph of the recycled-basis eigen phase of R4SVD (see r4svd_run), with
+// what its recorded launches depend on.
+struct EigGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<Pending> scopes;  // profiler events recorded inside the graph
+  int64_t launches = 0;         // kernels per launch of the graph
+  int r = -1;
+  const void *Q = nullptr, *Bt = nullptr, *Unew = nullptr;
+  bool prof = false;
+  uint64_t used = 0;
+  EigGraph() = default;
+  EigGraph(const EigGraph&) = delete;
+  EigGraph& operator=(const EigGraph&) = delete;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);  // an in-flight graph is freed on completion
+    exec = nullptr;
+    for (auto& e : scopes) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    scopes.clear();
+    r = -1;
+  }
+  ~EigGraph() { reset(); }
+};
+
 template <typename T>
 struct Work {
   Params P;
@@ -218,6 +265,26 @@ struct Work {
   double *pv = nullptr, *pu = nullptr, *pw = nullptr;  // power-iteration vectors
   unsigned* flags = nullptr;
   void* spmm_scr = nullptr;         // partial rows of the entry-chunked SpMM
+  // Set by a caller whose sampled update already formed Bt = Y^T Q for the s recycled
+  // columns (the fused update); r4svd_run then skips that product and clears it.
+  bool bt_ready = false;
+  // Non-null: this CSR copy of Y is stale (the fused update wrote only the CSC copy);
+  // r4svd_run refreshes it from y_csc before its first CSR product and clears it.
+  T* y_csr_stale = nullptr;
+  // Recycled iterations replay the eigen phase as a captured graph (two graphs: the basis
+  // and B^T buffers alternate); host_pin is page-locked host memory of pin_doubles()
+  // doubles for the graph's copies.  Off unless the caller provides host_pin.
+  double* host_pin = nullptr;
+  bool graph_broken = false;
+  uint64_t graph_clock = 0;
+  EigGraph eg[2];
+  // graphs are recorded on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured) and launched on the caller's
+  struct OwnedStream {
+    cudaStream_t s = nullptr;
+    ~OwnedStream() { if (s) cudaStreamDestroy(s); }
+  } cap;
+  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + 8; }
 
   void layout(Arena& a) {
     const int64_t m = P.m, n = P.n, z = pat->nnz;
@@ -290,6 +357,187 @@ struct R4Out {
 // Algorithm 3 (Algorithm 2 when s == 0).  Q holds the recycled basis in columns [0, s);
 // new blocks are appended in place.  On return U = Q U_B is written to Unew (m x ldq),
 // Bt (n x r) = Y^T Q, W.Ub = U_B, sigma on the host.
+enum class EigFrom {
+  kClusters,  // near-diagonal cluster start, checked refinement, second pass, else Jacobi
+  kRejected,  // the checked refinement from the cluster start was refused: second pass
+  kJacobi,    // full binary32 Jacobi, then refinement
+};
+
+// svt(B): eigen-decomposition of G = B B^T = (B^T)^T B^T (formed here when gram is set),
+// U = Q U_B and sigma on the host.  A purely recycled basis (no new block) leaves G
+// nearly diagonal: the binary64 refinement starts from the identity with the coupled
+// clusters diagonalised, and the result is accepted only if no coupled pair was left;
+// otherwise (or if a cluster is too large) it starts from the full binary32 Jacobi.
+template <typename T>
+svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram, R4Out* o) {
+  const int64_t m = W.P.m, n = W.P.n;
+  const int sv = (int)sizeof(T);
+  cudaStream_t st = W.s;
+  if (gram) {
+    SVT_PROF("gram_B", gemm_bytes(n, r, 0, sv, false), st);
+    SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
+  }
+  bool near_diagonal = false;
+  int status = 1;
+  if (from == EigFrom::kClusters) {
+    {
+      SVT_PROF("eig_cluster", 8.0 * r * r, st);
+      SVT_TRY(eig_start_clusters(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 3)));
+    }
+    SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaStreamSynchronize(st));
+    if (status != 0) prof_count("eig_start_oversize");
+    if (status == 0) {
+      {
+        SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+        SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, near_diagonal_steps<T>(), st,
+                           reinterpret_cast<int*>(W.flags + 3), near_diagonal_tol<T>()));
+      }
+      SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SVT_CUDA(cudaStreamSynchronize(st));
+      if (status != 0) from = EigFrom::kRejected;
+      else near_diagonal = true;
+    }
+  }
+  if (from == EigFrom::kRejected) {
+    // an unresolved pair: resolve its cluster in the rotated basis, once
+    prof_count("eig_start_rejected");
+    {
+      SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+      SVT_TRY(eig_refine_clusters_again(r, W.G, r, W.lam, W.Ub, r, W.eigw, 2, st,
+                                        reinterpret_cast<int*>(W.flags + 3),
+                                        near_diagonal_tol<T>()));
+    }
+    SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaStreamSynchronize(st));
+    if (status != 0) prof_count("eig_start_rejected_twice");
+    near_diagonal = status == 0;  // else redo from the full Jacobi
+  }
+  if (!near_diagonal) {
+    {
+      SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
+      SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2)));
+    }
+    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
+  }
+  std::vector<double> lam(r);
+  SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // U = Q U_B (all r columns are recycled)
+  {
+    SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
+    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+  }
+  SVT_CUDA(cudaStreamSynchronize(st));
+  prof_flush();
+  if (g_prof_on && !near_diagonal) {  // sweep count of the binary32 Jacobi stage (pseudo-entry)
+    int sweeps = 0;
+    if (cudaMemcpy(&sweeps, W.flags + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      const int id = prof_id("jacobi_sweeps");
+      g_prof[id].launches += 1;
+      g_prof[id].bytes += sweeps;
+    }
+  }
+  o->sigma.assign(r, 0.0);
+  for (int j = 0; j < r; ++j) {
+    if (!std::isfinite(lam[j])) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
+    o->sigma[j] = std::sqrt(std::max(lam[j], 0.0));
+  }
+  return SVT_OK;
+}
+
+// The eigen phase of a purely recycled basis, enqueued without host synchronisation so
+// that it can be captured: ||B||_F^2 by columns (copied to host_pin[0, r)), G = B B^T, the
+// near-diagonal cluster start (identity if a cluster is too large, status in flags[1]),
+// the checked binary64 refinement (status in flags[3]), the status words and the
+// eigenvalues copied to host_pin, and U = Q U_B.
+template <typename T>
+svt_status eig_phase_enqueue(Work<T>& W, T* Q, int r, T* Unew) {
+  const int64_t m = W.P.m, n = W.P.n;
+  const int sv = (int)sizeof(T);
+  cudaStream_t st = W.s;
+  SVT_TRY(colsumsq<T>(n, r, W.Bt, W.ldb, W.colss, W.part, st));
+  SVT_CUDA(cudaMemcpyAsync(W.host_pin, W.colss, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  {
+    SVT_PROF("gram_B", gemm_bytes(n, r, 0, sv, false), st);
+    SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
+  }
+  {
+    SVT_PROF("eig_cluster", 8.0 * r * r, st);
+    SVT_TRY(eig_start_clusters(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 1), true));
+  }
+  {
+    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, near_diagonal_steps<T>(), st,
+                       reinterpret_cast<int*>(W.flags + 3), near_diagonal_tol<T>()));
+  }
+  SVT_CUDA(cudaMemcpyAsync(W.host_pin + r, W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SVT_CUDA(cudaMemcpyAsync(W.host_pin + 2 * r, W.flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  {
+    SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
+    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+  }
+  return SVT_OK;
+}
+
+// Launches eig_phase_enqueue as a graph, capturing it first when no cached graph matches
+// (r, the buffers, the profiler state).  *ran = false when capture is unavailable; the
+// caller then runs the phase eagerly.
+template <typename T>
+svt_status eig_phase_graph(Work<T>& W, T* Q, int r, T* Unew, bool* ran) {
+  *ran = false;
+  if (W.graph_broken || !W.host_pin) return SVT_OK;
+  cudaStream_t st = W.s;
+  EigGraph* g = nullptr;
+  for (auto& c : W.eg)
+    if (c.exec && c.r == r && c.Q == Q && c.Bt == W.Bt && c.Unew == Unew && c.prof == g_prof_on) g = &c;
+  if (!g) {
+    g = W.eg[0].used <= W.eg[1].used ? &W.eg[0] : &W.eg[1];
+    g->reset();
+    SVT_TRY(eig_prepare());
+    if (!W.cap.s) SVT_CUDA(cudaStreamCreateWithFlags(&W.cap.s, cudaStreamNonBlocking));
+    std::vector<Pending> scopes;
+    const int64_t l0 = launches_so_far();
+    SVT_CUDA(cudaStreamBeginCapture(W.cap.s, cudaStreamCaptureModeThreadLocal));
+    g_prof_capture = &scopes;
+    W.s = W.cap.s;
+    const svt_status es = eig_phase_enqueue<T>(W, Q, r, Unew);
+    W.s = st;
+    g_prof_capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(W.cap.s, &graph);
+    const int64_t recorded = launches_so_far() - l0;
+    count_launches(-recorded);  // counted when the graph runs
+    cudaError_t ie = cudaErrorUnknown;
+    if (es == SVT_OK && ce == cudaSuccess && graph) ie = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {  // leave graphs off for this solve and run eagerly
+      for (auto& e : scopes) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+      g->exec = nullptr;
+      cudaGetLastError();
+      W.graph_broken = true;
+      prof_count("eig_graph_unavailable");
+      return SVT_OK;
+    }
+    g->scopes = std::move(scopes);
+    g->launches = recorded;
+    g->r = r; g->Q = Q; g->Bt = W.Bt; g->Unew = Unew; g->prof = g_prof_on;
+  }
+  g->used = ++W.graph_clock;
+  SVT_CUDA(cudaGraphLaunch(g->exec, st));
+  count_launches(g->launches);
+  if (g->prof) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const auto& e : g->scopes) g_pending.push_back(e);
+  }
+  *ran = true;
+  return SVT_OK;
+}
+
+// Algorithm 3 (Algorithm 2 when s == 0).  Q holds the recycled basis in columns [0, s);
+// new blocks are appended in place.  On return U = Q U_B is written to Unew (m x ldq),
+// Bt (n x r) = Y^T Q, W.Ub = U_B, sigma on the host.
 template <typename T>
 svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, double normY2,
                      double eps_thr, uint32_t iter, T* Unew, R4Out* o) {
@@ -301,14 +549,49 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   double normB = 0.0;
   const int sv = (int)sizeof(T);
   const int64_t z = p->nnz;
-  if (s > 0) {
-    {
+  auto eps_of = [&](double nb) { return normY2 > 0.0 ? (normY2 - nb) / normY2 : 0.0; };
+  // A recycled basis whose B^T the fused update already formed usually needs no new block:
+  // run the whole eigen phase as one graph and check that assumption afterwards.
+  bool have_normB = false;
+  if (s > 0 && W.bt_ready) {
+    bool ran = false;
+    SVT_TRY(eig_phase_graph<T>(W, Q, s, Unew, &ran));
+    if (ran) {
+      have_normB = true;
+      SVT_CUDA(cudaStreamSynchronize(st));
+      prof_flush();
+      const double* hp = W.host_pin;
+      for (int c = 0; c < s; ++c) normB += hp[c];
+      const double eps0 = eps_of(normB);
+      if (!(eps0 > eps_thr && s < P.r_cap)) {  // no new block: the graph's results stand
+        unsigned fl[4];
+        memcpy(fl, hp + 2 * s, sizeof(fl));
+        o->r = s; o->blocks = 0; o->exhausted = false; o->eps = eps0; o->normB = normB;
+        o->sigma.assign(s, 0.0);
+        if (fl[1] == 0 && fl[3] == 0) {
+          for (int j = 0; j < s; ++j) {
+            const double lj = hp[s + j];
+            if (!std::isfinite(lj)) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
+            o->sigma[j] = std::sqrt(std::max(lj, 0.0));
+          }
+          return SVT_OK;
+        }
+        if (fl[1] != 0) prof_count("eig_start_oversize");
+        // the near-diagonal start was refused: finish eagerly from G (already formed)
+        return eig_finish<T>(W, Q, s, Unew, fl[1] != 0 ? EigFrom::kJacobi : EigFrom::kRejected,
+                             false, o);
+      }
+      // the basis must grow: fall through with ||B||^2 known (G and U are redone below)
+    }
+  }
+  if (s > 0 && !have_normB) {
+    if (!W.bt_ready) {
       SVT_PROF("spmm_csc_recycled", spmm_bytes(z, n, m, s, sv), st);
       SVT_TRY((launch_spmm_rows<T, T>(n, p->col_ptr, p->row_idx, y_csc, Q, W.ldq, s, W.Bt, W.ldb, W.spmm_scr, z, st, p->chunk_row_csc)));
     }
     SVT_TRY(block_sumsq<T>(W, n, s, W.Bt, W.ldb, &normB));
   }
-  auto eps_of = [&](double nb) { return normY2 > 0.0 ? (normY2 - nb) / normY2 : 0.0; };
+  W.bt_ready = false;
   double eps = eps_of(normB);
   bool first = (s == 0);
   int blocks = 0;
@@ -320,6 +603,11 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
       SVT_TRY(launch_gaussian<T>(P.seed, iter, (uint32_t)blocks, n, w, W.Om, W.ldw, st));
     }
     ++blocks;
+    if (W.y_csr_stale) {
+      SVT_PROF("scatter_csr", (double)z * (4 + 2 * sv), st);
+      SVT_TRY(launch_scatter<T>(z, p->perm, y_csc, W.y_csr_stale, st));
+      W.y_csr_stale = nullptr;
+    }
     {
       SVT_PROF("spmm_csr", spmm_bytes(z, m, n, w, sv), st);
       SVT_TRY((launch_spmm_rows<T, T>(m, p->row_ptr, p->col_idx, y_csr, W.Om, W.ldw, w, W.X, W.ldw, W.spmm_scr, z, st, p->chunk_row_csr)));
@@ -381,77 +669,8 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   o->r = r; o->blocks = blocks; o->exhausted = exhausted; o->eps = eps; o->normB = normB;
   o->sigma.assign(r, 0.0);
   if (r == 0) return SVT_OK;
-  // svt(B): eigen-decomposition of B B^T = (B^T)^T B^T
-  {
-    SVT_PROF("gram_B", gemm_bytes(n, r, 0, sv, false), st);
-    SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
-  }
-  // A purely recycled basis (no new block) leaves G nearly diagonal: start the binary64
-  // refinement from the identity with the coupled clusters diagonalised, and accept the
-  // result only if no coupled pair was left; otherwise (or if a cluster is too large)
-  // start from the full binary32 Jacobi.
-  bool near_diagonal = false;
-  if (s > 0 && blocks == 0) {
-    int status = 1;
-    {
-      SVT_PROF("eig_cluster", 8.0 * r * r, st);
-      SVT_TRY(eig_start_clusters(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 3)));
-    }
-    SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SVT_CUDA(cudaStreamSynchronize(st));
-    if (status != 0) prof_count("eig_start_oversize");
-    if (status == 0) {
-      {
-        SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
-        SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, near_diagonal_steps<T>(), st,
-                           reinterpret_cast<int*>(W.flags + 3), near_diagonal_tol<T>()));
-      }
-      SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-      SVT_CUDA(cudaStreamSynchronize(st));
-      if (status != 0) {  // an unresolved pair: resolve its cluster in the rotated basis, once
-        prof_count("eig_start_rejected");
-        SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
-        SVT_TRY(eig_refine_clusters_again(r, W.G, r, W.lam, W.Ub, r, W.eigw, 2, st,
-                                          reinterpret_cast<int*>(W.flags + 3),
-                                          near_diagonal_tol<T>()));
-        SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-        SVT_CUDA(cudaStreamSynchronize(st));
-        if (status != 0) prof_count("eig_start_rejected_twice");
-      }
-      near_diagonal = status == 0;  // else redo from the full Jacobi
-    }
-  }
-  if (!near_diagonal) {
-    {
-      SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
-      SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2)));
-    }
-    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
-    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
-  }
-  std::vector<double> lam(r);
-  SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
-  // U = Q U_B (all r columns are recycled)
-  {
-    SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
-    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
-  }
-  SVT_CUDA(cudaStreamSynchronize(st));
-  prof_flush();
-  if (g_prof_on && !near_diagonal) {  // sweep count of the binary32 Jacobi stage (pseudo-entry)
-    int sweeps = 0;
-    if (cudaMemcpy(&sweeps, W.flags + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) {
-      std::lock_guard<std::mutex> lk(g_prof_mu);
-      const int id = prof_id("jacobi_sweeps");
-      g_prof[id].launches += 1;
-      g_prof[id].bytes += sweeps;
-    }
-  }
-  for (int j = 0; j < r; ++j) {
-    if (!std::isfinite(lam[j])) return fail(SVT_ERR_NUMERIC, "R4SVD: non-finite eigenvalue");
-    o->sigma[j] = std::sqrt(std::max(lam[j], 0.0));
-  }
-  return SVT_OK;
+  return eig_finish<T>(W, Q, r, Unew, s > 0 && blocks == 0 ? EigFrom::kClusters : EigFrom::kJacobi,
+                       true, o);
 }
 
 // Wk (n x k) = Bt (n x r) * Ub[:, :k] diag(coef).  Columns k .. round_up(k, 4) - 1 of Wk

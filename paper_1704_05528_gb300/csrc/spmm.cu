@@ -192,6 +192,14 @@ __global__ void k_gather(int64_t count, const int32_t* __restrict__ perm, const 
     dst[q] = src[perm[q]];
 }
 
+template <typename T>
+__global__ void k_scatter(int64_t count, const int32_t* __restrict__ perm, const T* __restrict__ src,
+                          T* __restrict__ dst) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
+       q += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[q]] = src[q];
+}
+
 __global__ void k_zero_rows(int64_t nrows, int w, void* out_, int64_t ldo, int elem) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nrows * w;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -309,6 +317,39 @@ svt_status launch_gather(int64_t count, const int32_t* perm, const T* src, T* ds
   return SVT_OK;
 }
 
+template <typename T>
+svt_status launch_scatter(int64_t count, const int32_t* perm, const T* src, T* dst,
+                          cudaStream_t s) {
+  if (count <= 0) return SVT_OK;
+  int64_t g = ceil_div(count, 256);
+  const int64_t cap = (int64_t)num_sms() * 32;
+  if (g > cap) g = cap;
+  k_scatter<T><<<(int)g, 256, 0, s>>>(count, perm, src, dst);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+template <typename TD>
+void spmm_slots(void* scratch, int64_t nnz, int w, TD** part, int64_t* ldp, int32_t** tails) {
+  const int64_t nchunks = ceil_div(nnz, chunk_size(nnz));
+  *part = reinterpret_cast<TD*>(scratch);
+  *ldp = round_up(w, 4);
+  *tails = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(scratch) +
+                                      part_bytes(nchunks, w, (int)sizeof(TD)));
+}
+
+template <typename TD>
+svt_status spmm_fixup(int64_t nnz, const int32_t* ptr, const TD* part, int64_t ldp,
+                      const int32_t* tails, int w, TD* out, int64_t ldo, cudaStream_t s) {
+  if (nnz <= 0 || w <= 0) return SVT_OK;
+  const int64_t C = chunk_size(nnz);
+  const int64_t nchunks = ceil_div(nnz, C);
+  k_spmm_fixup<TD><<<(int)ceil_div(nchunks, 8), 256, 0, s>>>(nchunks, C, ptr, part, ldp, tails, w,
+                                                              out, ldo);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
 #define SVT_INST_SPMM(TV, TD)                                                                   \
   template svt_status launch_spmm_rows<TV, TD>(int64_t, const int32_t*, const int32_t*,          \
                                                const TV*, const TD*, int64_t, int, TD*, int64_t, \
@@ -320,5 +361,15 @@ template svt_status launch_gather<double>(int64_t, const int32_t*, const double*
                                           cudaStream_t);
 template svt_status launch_gather<float>(int64_t, const int32_t*, const float*, float*,
                                          cudaStream_t);
+template svt_status launch_scatter<double>(int64_t, const int32_t*, const double*, double*,
+                                           cudaStream_t);
+template svt_status launch_scatter<float>(int64_t, const int32_t*, const float*, float*,
+                                          cudaStream_t);
+template void spmm_slots<double>(void*, int64_t, int, double**, int64_t*, int32_t**);
+template void spmm_slots<float>(void*, int64_t, int, float**, int64_t*, int32_t**);
+template svt_status spmm_fixup<double>(int64_t, const int32_t*, const double*, int64_t,
+                                       const int32_t*, int, double*, int64_t, cudaStream_t);
+template svt_status spmm_fixup<float>(int64_t, const int32_t*, const float*, int64_t,
+                                      const int32_t*, int, float*, int64_t, cudaStream_t);
 
 }  // namespace svt

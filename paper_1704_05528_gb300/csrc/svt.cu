@@ -58,6 +58,8 @@ svt_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 int num_sms() {
   static int cached = 0;
@@ -102,6 +104,7 @@ svt_status DeviceBlock::alloc(size_t bytes, cudaStream_t s) {
 // profiler state shared with solver.cuh
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+thread_local std::vector<Pending>* g_prof_capture = nullptr;
 std::vector<ProfEntry> g_prof;
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
@@ -174,17 +177,34 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     return SVT_OK;
   }
 
+  // page-locked host words for the copies inside the captured eigen phase
+  struct HostPin {
+    void* p = nullptr;
+    ~HostPin() { if (p) cudaFreeHost(p); }
+  } pin;
+  SVT_CUDA(cudaMallocHost(&pin.p, Work<T>::pin_doubles(P.r_cap) * sizeof(double)));
   Work<T> W;
   W.P = P; W.pat = pat; W.s = st;
+  W.host_pin = static_cast<double*>(pin.p);
+  // A and Y in both orders, and a second B^T that the fused update fills while the
+  // solver still reads the current one
+  const int64_t ldb_alt = ld_of(P.r_cap);
+  auto take_own = [&](Arena& ar, T** a_csr_, T** y_csr_, T** a_csc_, T** bt_alt_, double** fpart_) {
+    *a_csr_ = ar.take<T>(nnz);
+    *y_csr_ = ar.take<T>(nnz);
+    *a_csc_ = ar.take<T>(nnz);
+    *bt_alt_ = ar.take<T>(n * ldb_alt);
+    *fpart_ = ar.take<double>(update_recycle_scratch(nnz));
+  };
+  T *a_csr, *y_csr, *a_csc, *bt_alt;
+  double* fpart;
   Arena a;
-  T* a_csr = a.take<T>(nnz);
-  T* y_csr = a.take<T>(nnz);
+  take_own(a, &a_csr, &y_csr, &a_csc, &bt_alt, &fpart);
   W.layout(a);
   DeviceBlock wblk;
   SVT_TRY(wblk.alloc(a.off, st));
   Arena b; b.base = (char*)wblk.ptr;
-  a_csr = b.take<T>(nnz);
-  y_csr = b.take<T>(nnz);
+  take_own(b, &a_csr, &y_csr, &a_csc, &bt_alt, &fpart);
   W.layout(b);
   SVT_CUDA(cudaMemsetAsync(W.flags, 0, 4 * sizeof(unsigned), st));
 
@@ -203,8 +223,8 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   }
   const double nA = std::sqrt(nA2);
 
-  // ||P_Lambda(A)||_2 by power steps v <- A^T A v / ||A^T A v|| (a_csc staged in y_csc)
-  SVT_TRY(launch_gather<T>(nnz, pat->perm, a_csr, W.y_csc, st));
+  // ||P_Lambda(A)||_2 by power steps v <- A^T A v / ||A^T A v||
+  SVT_TRY(launch_gather<T>(nnz, pat->perm, a_csr, a_csc, st));
   SVT_TRY(launch_gaussian<double>(P.seed, kPowerSeedIter, 0, n, 1, W.pw, 1, st));
   SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
   k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
@@ -213,7 +233,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     SVT_PROF("init_power", spmm_bytes(nnz, m, n, 1, (int)sizeof(T)) + spmm_bytes(nnz, n, m, 1, (int)sizeof(T)), st);
     SVT_TRY((launch_spmm_rows<T, double>(m, pat->row_ptr, pat->col_idx, a_csr, W.pv, 1, 1, W.pu, 1,
                                          W.spmm_scr, nnz, st, pat->chunk_row_csr)));
-    SVT_TRY((launch_spmm_rows<T, double>(n, pat->col_ptr, pat->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1,
+    SVT_TRY((launch_spmm_rows<T, double>(n, pat->col_ptr, pat->row_idx, a_csc, W.pu, 1, 1, W.pw, 1,
                                          W.spmm_scr, nnz, st, pat->chunk_row_csc)));
     SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
     k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
@@ -244,8 +264,13 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   int last_iter = 0;
   svt_status status = SVT_NOT_CONVERGED;
   std::vector<double> coef;
+  bool fused = false;
   for (int i = 1; i <= maxit; ++i) {
     const auto t_it = clk::now();
+    if (fused) {  // the last update formed Y^T U for this iteration's recycled basis
+      std::swap(W.Bt, bt_alt);
+      W.bt_ready = true;
+    }
     SVT_TRY(r4svd_run<T>(W, y_csr, W.y_csc, Qcur, s, normY2, eps_thr, (uint32_t)i, Qnext, &ro));
     const int r = ro.r;
     k = 0;
@@ -254,7 +279,19 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     for (int j = 0; j < k; ++j) coef[j] = (ro.sigma[j] - tau) / ro.sigma[j];
     SVT_TRY(scaled_right<T>(W, r, k, coef));
     SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
-    {
+    // U (= Qnext, r columns) is the next iteration's recycled basis: in CSC order the
+    // update also forms B^T = Y^T U for it
+    fused = update_recycle_fits<T>(r, nnz);
+    if (fused) {
+      SVT_PROF("update_recycled", recycle_bytes(nnz, m, n, k, r, (int)sizeof(T)), st);
+      SVT_TRY(update_recycle<T>(pat, Qnext, W.ldq, r, W.Wk, W.ldk, k, a_csc, W.y_csc, delta, bt_alt,
+                                ldb_alt, W.dsc + 5, fpart, W.flags, W.spmm_scr, st));
+      W.y_csr_stale = y_csr;
+    } else {
+      if (W.y_csr_stale) {
+        SVT_TRY(launch_scatter<T>(nnz, pat->perm, W.y_csc, y_csr, st));
+        W.y_csr_stale = nullptr;
+      }
       SVT_PROF("sampled_update", update_bytes(nnz, m, n, k, (int)sizeof(T)), st);
       SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
                                 W.part, W.flags, st, true));
@@ -282,8 +319,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     }
     res->r = r;
     if (rel < tol) { status = SVT_OK; break; }
-    // Y^(i+1) is already in y_csr (the update ran in the fused pass); refresh its CSC copy
-    {
+    if (!fused) {  // Y^(i+1) is in y_csr; refresh its CSC copy
       SVT_PROF("gather_csc", (double)nnz * (4 + 2 * sizeof(T)), st);
       SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
     }
@@ -459,6 +495,48 @@ extern "C" svt_status svt_sampled_update(const svt_pattern* p, int precision, co
                                   (const float*)a_csr, (float*)y_csr, delta, out3, part, flags, s));
   else
     return fail(SVT_ERR_ARG, "sampled_update: unknown precision");
+  SVT_CUDA(cudaMemcpyAsync(sums, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SVT_CUDA(cudaStreamSynchronize(s));
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_sampled_update_recycle(const svt_pattern* p, int precision,
+                                                 const void* U, int64_t ldu, int32_t r,
+                                                 const void* W, int64_t ldw, int32_t k,
+                                                 const void* a_csc, void* y_csc, double delta,
+                                                 void* Bt, int64_t ldb, double* sums,
+                                                 void* stream) {
+  using namespace svt;
+  if (!p || !sums || !U || !Bt || r < 1 || k < 0 || k > r || ldb < r || ldu < r ||
+      (k > 0 && (!W || ldw < k)) || (p->nnz > 0 && (!a_csc || !y_csc)))
+    return fail(SVT_ERR_ARG, "sampled_update_recycle: bad arguments");
+  if (precision != SVT_FP64 && precision != SVT_MIXED_FP32)
+    return fail(SVT_ERR_ARG, "sampled_update_recycle: unknown precision");
+  const bool f64 = precision == SVT_FP64;
+  if (!(f64 ? update_recycle_fits<double>(r, p->nnz) : update_recycle_fits<float>(r, p->nnz)))
+    return fail(SVT_ERR_ARG, "sampled_update_recycle: r = %d or nnz above the limit", r);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t z = p->nnz;
+  const size_t pe = update_recycle_scratch(z);
+  const size_t sb = spmm_scratch_bytes(z > 0 ? z : 1, r, f64 ? 8 : 4);
+  DeviceBlock blk;
+  SVT_TRY(blk.alloc(round_up((int64_t)(pe * sizeof(double)), 256) + 256 + sb, s));
+  double* part = (double*)blk.ptr;
+  double* out3 = (double*)((char*)blk.ptr + round_up((int64_t)(pe * sizeof(double)), 256));
+  unsigned* flags = (unsigned*)(out3 + 4);
+  void* scratch = (char*)out3 + 256;
+  SVT_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
+  // W is only read when k > 0; a k = 0 call may pass any aligned pointer for it
+  const void* Wp = k > 0 ? W : U;
+  const int64_t ldw_ = k > 0 ? ldw : ldu;
+  if (f64)
+    SVT_TRY(update_recycle<double>(p, (const double*)U, ldu, r, (const double*)Wp, ldw_, k,
+                                   (const double*)a_csc, (double*)y_csc, delta, (double*)Bt, ldb,
+                                   out3, part, flags, scratch, s));
+  else
+    SVT_TRY(update_recycle<float>(p, (const float*)U, ldu, r, (const float*)Wp, ldw_, k,
+                                  (const float*)a_csc, (float*)y_csc, delta, (float*)Bt, ldb, out3,
+                                  part, flags, scratch, s));
   SVT_CUDA(cudaMemcpyAsync(sums, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   SVT_CUDA(cudaStreamSynchronize(s));
   return SVT_OK;

@@ -203,6 +203,162 @@ k_sampled_update(int64_t nnz, int64_t C, int64_t nchunks, const int32_t* __restr
   }
 }
 
+// The same update in CSC order, fused with the next iteration's recycled product.
+// R4SVD recycles the basis U that defines X (Algorithm 3), so B^T = Y_new^T U (eq. (5)
+// gives Y_new) can be formed while the update holds the rows of U it gathers: each entry
+// (p, q) gathers U[p, :r] once, dots its first k columns with W[q, :k] (held in registers
+// while the warp stays in column q), writes Y_pq += delta (A_pq - x_pq) and adds
+// Y_pq(new) U[p, :r] into row q of B^T.  Chunks, groups and the partial rows of columns
+// that cross chunks follow launch_spmm_rows (head and tail slots, then the fix-up in chunk
+// order), so B^T does not depend on scheduling.  The loop over a column's entries has the
+// same trip count in every group of the warp (the group reductions need all lanes).
+template <typename T, int VEC, int G, int MAXV, int UNR, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_update_recycle(int32_t n, int32_t nnz, int32_t C, int32_t nchunks,
+                 const int32_t* __restrict__ col_ptr, const int32_t* __restrict__ row_idx,
+                 const int32_t* __restrict__ chunk_col, const T* __restrict__ U, int64_t ldu,
+                 int r, const T* __restrict__ W, int64_t ldw, int k, const T* __restrict__ a,
+                 T* __restrict__ y, T delta, T* __restrict__ bt, int64_t ldb,
+                 T* __restrict__ slots, int64_t ldp, int32_t* __restrict__ tail_col,
+                 double* __restrict__ part, unsigned* __restrict__ flags) {
+  constexpr int NG = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane % G;
+  // entry offsets fit in int32: the pattern's column pointers are int32
+  const int32_t chunk = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  SumAcc<T> acc_d2, acc_abs, acc_y2;
+  bool bad = false;
+  if (chunk < nchunks) {  // warp-uniform
+    const int32_t beg = chunk * C;
+    const int32_t end = (nnz - beg > C) ? beg + C : nnz;
+    const bool last_chunk = (chunk == nchunks - 1);
+    int32_t my_tail = -1;
+    for (int32_t q = chunk_col[chunk]; q < n; ++q) {
+      const int32_t cb = col_ptr[q], ce = col_ptr[q + 1];
+      if (cb >= end && !(last_chunk && cb == nnz)) break;
+      const int32_t sb = cb > beg ? cb : beg;
+      const int32_t se = ce < end ? ce : end;
+      // this lane's slices of W[q, :k], zero from column k on
+      T wq[MAXV][VEC];
+#pragma unroll
+      for (int t = 0; t < MAXV; ++t) {
+        const int c0 = (gl + t * G) * VEC;
+        if (c0 < k) load_v<T, VEC>(W + (int64_t)q * ldw + c0, wq[t]);
+#pragma unroll
+        for (int b = 0; b < VEC; ++b)
+          if (c0 + b >= k) wq[t][b] = T(0);
+      }
+      T acc[MAXV][VEC];
+#pragma unroll
+      for (int t = 0; t < MAXV; ++t)
+#pragma unroll
+        for (int b = 0; b < VEC; ++b) acc[t][b] = T(0);
+      for (int32_t e0 = sb + grp; e0 - grp < se; e0 += NG * UNR) {
+        T av[UNR], yv[UNR];
+        T ux[UNR][MAXV][VEC];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) {
+          const int32_t e = e0 + j * NG;
+          const bool v = e < se;
+          const T* up = U + (int64_t)(v ? row_idx[e] : 0) * ldu;
+          av[j] = v ? a[e] : T(0);
+          yv[j] = v ? y[e] : T(0);
+#pragma unroll
+          for (int t = 0; t < MAXV; ++t) {
+            const int c0 = (gl + t * G) * VEC;
+            if (v && c0 < r) load_v<T, VEC>(up + c0, ux[j][t]);
+#pragma unroll
+            for (int b = 0; b < VEC; ++b)
+              if (!v || c0 + b >= r) ux[j][t][b] = T(0);
+          }
+        }
+        T px[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) {
+          px[j] = T(0);
+#pragma unroll
+          for (int t = 0; t < MAXV; ++t)
+#pragma unroll
+            for (int b = 0; b < VEC; ++b) px[j] = fma(ux[j][t][b], wq[t][b], px[j]);
+        }
+        // butterfly over the group: every lane ends with the same sum (a + b == b + a)
+#pragma unroll
+        for (int j = 0; j < UNR; ++j)
+#pragma unroll
+          for (int o = 1; o < G; o <<= 1) px[j] += __shfl_xor_sync(0xffffffffu, px[j], o);
+        // every lane forms all UNR updated values (zero for a masked entry) ...
+        T yn[UNR], d[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; ++j) {
+          d[j] = av[j] - px[j];
+          yn[j] = fma(delta, d[j], yv[j]);
+        }
+        // ... and lane j0 + l of the group stores entry j0 + l and adds it to the sums,
+        // so the group's entries finish in one instruction stream
+#pragma unroll
+        for (int j0 = 0; j0 < UNR; j0 += G) {
+          T ds = T(0), ys = T(0);
+          bool vs = false;
+#pragma unroll
+          for (int j = j0; j < UNR && j < j0 + G; ++j)
+            if (gl == j - j0) { ds = d[j]; ys = yn[j]; vs = e0 + j * NG < se; }
+          if (vs) {
+            y[e0 + (j0 + gl) * NG] = ys;
+            acc_d2.add_sq(ds);
+            acc_abs.add(fabs(ds));
+            acc_y2.add_sq(ys);
+            bad |= !isfinite(ys);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; ++j)
+#pragma unroll
+          for (int t = 0; t < MAXV; ++t)
+#pragma unroll
+            for (int b = 0; b < VEC; ++b) acc[t][b] = fma(yn[j], ux[j][t][b], acc[t][b]);
+      }
+#pragma unroll
+      for (int t = 0; t < MAXV; ++t)
+#pragma unroll
+        for (int b = 0; b < VEC; ++b)
+#pragma unroll
+          for (int o = G; o < 32; o <<= 1) acc[t][b] += __shfl_xor_sync(0xffffffffu, acc[t][b], o);
+      T* dst;
+      if (cb >= beg && ce <= end) {
+        dst = bt + (int64_t)q * ldb;
+      } else if (cb < beg) {
+        dst = slots + (int64_t)(2 * chunk) * ldp;      // head slot
+      } else {
+        dst = slots + (int64_t)(2 * chunk + 1) * ldp;  // tail slot
+        my_tail = q;
+      }
+      if (grp == 0) {
+#pragma unroll
+        for (int t = 0; t < MAXV; ++t) {
+          const int c0 = (gl + t * G) * VEC;
+#pragma unroll
+          for (int b = 0; b < VEC; ++b)
+            if (c0 + b < r) dst[c0 + b] = acc[t][b];
+        }
+      }
+    }
+    if (lane == 0) tail_col[chunk] = my_tail;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NONFINITE);
+  // one partial per chunk (fixed shuffle tree), summed in chunk order by k_finish; no
+  // block-wide barrier, so a warp leaves as soon as its chunk is done
+  if (chunk < nchunks) {
+    const double s_d2 = warp_sum(acc_d2.value());
+    const double s_abs = warp_sum(acc_abs.value());
+    const double s_y2 = warp_sum(acc_y2.value());
+    if (lane == 0) {
+      part[(int64_t)chunk * 3 + 0] = s_d2;
+      part[(int64_t)chunk * 3 + 1] = s_abs;
+      part[(int64_t)chunk * 3 + 2] = s_y2;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_sumsq_part(int64_t count, const T* __restrict__ x, double* __restrict__ part,
                              unsigned* __restrict__ flags) {
@@ -340,6 +496,94 @@ svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T
   return SVT_OK;
 }
 
+namespace {
+
+int64_t recycle_chunks(int64_t nnz) { return ceil_div(nnz, chunk_size(nnz)); }
+
+template <typename T, int VEC, int G, int MAXV, int UNR, int MINB>
+svt_status run_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, const T* W,
+                       int64_t ldw, int k, const T* a, T* y, double delta, T* bt, int64_t ldb,
+                       double* part, unsigned* flags, void* scratch, cudaStream_t s) {
+  const int64_t z = p->nnz;
+  const int64_t C = chunk_size(z);
+  const int64_t nchunks = ceil_div(z, C);
+  T* slots;
+  int64_t ldp;
+  int32_t* tails;
+  spmm_slots<T>(scratch, z, r, &slots, &ldp, &tails);
+  k_update_recycle<T, VEC, G, MAXV, UNR, MINB><<<(int)ceil_div(nchunks, 8), 256, 0, s>>>(
+      (int32_t)p->n, (int32_t)z, (int32_t)C, (int32_t)nchunks, p->col_ptr, p->row_idx, p->chunk_row_csc, U, ldu, r, W, ldw, k, a, y,
+      (T)delta, bt, ldb, slots, ldp, tails, part, flags);
+  SVT_LAUNCH_CHECK();
+  return spmm_fixup<T>(z, p->col_ptr, slots, ldp, tails, r, bt, ldb, s);
+}
+
+// Up to four vectors of U's row per lane, two entries in flight per group, as few lanes
+// per entry as that allows.  On the 71,567 x 10,681 pattern at r = 100 (binary32) this
+// shape (8 lanes per entry, 8 entries per warp, two blocks per SM) took 0.47 ms against
+// 0.60-0.98 ms for 16 or 32 lanes per entry, more entries in flight, or more blocks per SM
+// with fewer registers; prefetching the next step's indices gained nothing.
+template <typename T, int VEC>
+svt_status dispatch_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, const T* W,
+                            int64_t ldw, int k, const T* a, T* y, double delta, T* bt,
+                            int64_t ldb, double* part, unsigned* flags, void* scratch,
+                            cudaStream_t s) {
+  const int nv = (int)ceil_div(r, VEC);
+#define SVT_RUN(G) return run_recycle<T, VEC, G, 4, 2, 2>(p, U, ldu, r, W, ldw, k, a, y, delta, bt, ldb, part, flags, scratch, s)
+  if (nv <= 4) SVT_RUN(1);
+  if (nv <= 8) SVT_RUN(2);
+  if (nv <= 16) SVT_RUN(4);
+  if (nv <= 32) SVT_RUN(8);
+  if (nv <= 64) SVT_RUN(16);
+  SVT_RUN(32);
+#undef SVT_RUN
+}
+
+}  // namespace
+
+template <typename T>
+bool update_recycle_fits(int r, int64_t nnz) {
+  // entry offsets run in int32 with up to a chunk and a step of headroom
+  return r >= 1 && r <= (sizeof(T) == 4 ? 512 : 256) && nnz <= INT32_MAX - (int64_t)(1 << 16);
+}
+
+size_t update_recycle_scratch(int64_t nnz) {
+  return (size_t)(3 * recycle_chunks(nnz > 0 ? nnz : 1) + 8);
+}
+
+template <typename T>
+svt_status update_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, const T* W,
+                          int64_t ldw, int k, const T* a, T* y, double delta, T* bt, int64_t ldb,
+                          double* out3, double* part, unsigned* flags, void* scratch,
+                          cudaStream_t s) {
+  constexpr int V = sizeof(T) == 4 ? 4 : 2;
+  if (!update_recycle_fits<T>(r, p->nnz) || k < 0 || k > r)
+    return fail(SVT_ERR_UNSUPPORTED, "fused update: r = %d, k = %d", r, k);
+  if ((reinterpret_cast<uintptr_t>(U) % 16) || (ldu % V) || (reinterpret_cast<uintptr_t>(W) % 16) ||
+      (ldw % V) || ldw < round_up(k, V) || ldu < round_up(r, V))
+    return fail(SVT_ERR_UNSUPPORTED, "fused update: unaligned operands");
+  if (p->nnz == 0) {
+    SVT_CUDA(cudaMemsetAsync(out3, 0, 3 * sizeof(double), s));
+    if (p->n > 0) SVT_CUDA(cudaMemset2DAsync(bt, ldb * sizeof(T), 0, r * sizeof(T), p->n, s));
+    return SVT_OK;
+  }
+  SVT_TRY((dispatch_recycle<T, V>(p, U, ldu, r, W, ldw, k, a, y, delta, bt, ldb, part, flags,
+                                   scratch, s)));
+  k_finish<<<3, 256, 0, s>>>((int)recycle_chunks(p->nnz), 3, 3, part, out3);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+template bool update_recycle_fits<double>(int, int64_t);
+template bool update_recycle_fits<float>(int, int64_t);
+template svt_status update_recycle<double>(const svt_pattern*, const double*, int64_t, int,
+                                           const double*, int64_t, int, const double*, double*,
+                                           double, double*, int64_t, double*, double*, unsigned*,
+                                           void*, cudaStream_t);
+template svt_status update_recycle<float>(const svt_pattern*, const float*, int64_t, int,
+                                          const float*, int64_t, int, const float*, float*,
+                                          double, float*, int64_t, double*, double*, unsigned*,
+                                          void*, cudaStream_t);
 template svt_status sumsq<double>(int64_t, const double*, double*, double*, cudaStream_t);
 template svt_status sumsq<float>(int64_t, const float*, double*, double*, cudaStream_t);
 template svt_status scale_copy<double>(int64_t, const double*, double, double*, cudaStream_t);

@@ -18,7 +18,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = L.header_functions()
     for required in ("svt_complete", "svt_r4svd", "svt_pattern_create", "svt_pattern_destroy",
-                     "svt_spmm", "svt_sampled_update", "svt_gaussian_block"):
+                     "svt_spmm", "svt_sampled_update", "svt_sampled_update_recycle",
+                     "svt_gaussian_block"):
         assert required in names
 
 
@@ -60,6 +61,9 @@ def test_argument_validation_without_gpu(lib):
     assert b"tau" in lib.svt_last_error()
     h = C.c_void_p()
     assert lib.svt_pattern_create(-1, 3, 0, None, None, None, C.byref(h)) == L.SVT_ERR_ARG
+    sums = (C.c_double * 3)()
+    assert lib.svt_sampled_update_recycle(None, L.SVT_FP64, None, 4, 4, None, 4, 2, None, None, 1.0,
+                                          None, 4, sums, None) == L.SVT_ERR_ARG
 
 
 def test_unrolled_params_defaults_and_validation(lib):

@@ -175,6 +175,86 @@ def test_sampled_update_mixed(svt, torch_mod, k):
     assert math.isclose(sums[2], float(np.sum(y_ref * y_ref)), rel_tol=1e-5)
 
 
+def _recycle_case(rng, m, n):
+    """Heavy columns (40 columns holding 24,000 entries, each spanning many entry chunks),
+    an empty column range inside and at the end, scattered entries elsewhere."""
+    heavy = rng.choice(m * 40, size=24000, replace=False)
+    other_cols = np.setdiff1d(np.arange(40, n - 5), np.arange(512, 768))
+    flat_o = rng.choice(m * other_cols.size, size=36000, replace=False)
+    rows = np.concatenate([heavy // 40, flat_o // other_cols.size]).astype(np.int32)
+    cols = np.concatenate([heavy % 40, other_cols[flat_o % other_cols.size]]).astype(np.int32)
+    perm = rng.permutation(rows.size)
+    return rows[perm], cols[perm]
+
+
+def _recycle_reference(ref_p, n, U, Wm, a, y0, delta):
+    """Y_new in CSC order (eq. (5) on Lambda) and B^T = Y_new^T U, in binary64."""
+    import scipy.sparse as sp
+    k = Wm.shape[1]
+    cols = np.repeat(np.arange(n), np.diff(ref_p.col_ptr))
+    x = oracle.sampled_product(U[:, :k], np.ones(k), Wm, ref_p.row_idx, cols)
+    d = a - x
+    y_new = y0 + delta * d
+    Yt = sp.csr_matrix((y_new, (cols, ref_p.row_idx)), shape=(n, U.shape[0]))
+    bound = sp.csr_matrix((np.abs(y_new), (cols, ref_p.row_idx)), shape=(n, U.shape[0])) @ np.abs(U)
+    return y_new, d, Yt @ U, bound
+
+
+@pytest.mark.parametrize("r,k", [(100, 60), (8, 8), (130, 0), (256, 200), (1, 1)])
+def test_sampled_update_recycle(svt, torch_mod, r, k):
+    """The fused CSC-order update and recycled product against the binary64 definitions."""
+    rng = np.random.default_rng(31 + r + k)
+    m, n = 3001, 1300
+    rows, cols = _recycle_case(rng, m, n)
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    U = rng.standard_normal((m, r))
+    Wm = rng.standard_normal((n, k))
+    a = rng.standard_normal(ref_p.nnz)
+    y0 = rng.standard_normal(ref_p.nnz)
+    delta = 1.3
+    y_ref, d, bt_ref, bound = _recycle_reference(ref_p, n, U, Wm, a, y0, delta)
+    y_dev = torch_mod.from_numpy(y0.copy()).cuda()
+    Bt, sums = svt.sampled_update_recycle(P, torch_mod.from_numpy(U), torch_mod.from_numpy(Wm),
+                                          torch_mod.from_numpy(a), y_dev, delta)
+    assert _rel(y_dev.cpu().numpy(), y_ref) < 1e-14
+    assert np.all(np.abs(Bt.cpu().numpy() - bt_ref) <= 1e-13 * bound + 1e-300)
+    assert not np.any(Bt.cpu().numpy()[512:768]) and not np.any(Bt.cpu().numpy()[n - 5:])
+    assert math.isclose(sums[0], float(np.sum(d * d)), rel_tol=1e-12)
+    assert math.isclose(sums[1], float(np.sum(np.abs(d))), rel_tol=1e-12)
+    assert math.isclose(sums[2], float(np.sum(y_ref * y_ref)), rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("r,k", [(100, 60), (100, 100), (3, 2), (64, 33), (200, 128), (512, 300),
+                                 (130, 0)])
+def test_sampled_update_recycle_mixed(svt, torch_mod, r, k):
+    rng = np.random.default_rng(57 + r + k)
+    m, n = 3001, 1300
+    rows, cols = _recycle_case(rng, m, n)
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    f32 = lambda x: np.asarray(x, dtype=np.float32)
+    U = f32(rng.standard_normal((m, r)) / np.sqrt(r))
+    Wm = f32(rng.standard_normal((n, k)))
+    a = f32(rng.standard_normal(ref_p.nnz))
+    y0 = f32(rng.standard_normal(ref_p.nnz))
+    delta = 1.3
+    y_ref, d, bt_ref, bound = _recycle_reference(ref_p, n, U.astype(np.float64), Wm.astype(np.float64),
+                                                 a.astype(np.float64), y0.astype(np.float64), delta)
+    y_dev = torch_mod.from_numpy(y0.copy()).cuda()
+    Bt, sums = svt.sampled_update_recycle(P, torch_mod.from_numpy(U), torch_mod.from_numpy(Wm),
+                                          torch_mod.from_numpy(a), y_dev, delta, precision="mixed")
+    got = y_dev.cpu().numpy().astype(np.float64)
+    # binary32 dot of k terms: error below k ulps of sum |u w|, here (1 + sqrt(k)) delta 1e-5
+    assert np.max(np.abs(got - y_ref)) < 1e-5 * (1.0 + np.sqrt(k)) * delta
+    # each B^T element: binary32 sum over its column of y_new U, with y_new itself rounded
+    err = np.abs(Bt.cpu().numpy().astype(np.float64) - bt_ref)
+    assert np.all(err <= 1e-5 * (1.0 + np.sqrt(k)) * bound + 1e-30)
+    assert math.isclose(sums[0], float(np.sum(d * d)), rel_tol=1e-5)
+    assert math.isclose(sums[1], float(np.sum(np.abs(d))), rel_tol=1e-5)
+    assert math.isclose(sums[2], float(np.sum(y_ref * y_ref)), rel_tol=1e-5)
+
+
 # ------------------------------------------------------------------------ R4SVD
 def _sigma_close(got, ref, tol):
     got = np.asarray(got)
