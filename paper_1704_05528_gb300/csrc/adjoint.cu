@@ -383,7 +383,7 @@ svt_status rayleigh_ritz(Work<T>& W, const svt_pattern* pl, const T* y_csc, cons
   SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
   SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2)));
   SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
-  SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, U, W.ldq, st)));
+  SVT_TRY(lift_basis<T>(W, Q, r, U));
   std::vector<double> lam(r);
   SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
   SVT_CUDA(cudaStreamSynchronize(st));
@@ -623,7 +623,7 @@ svt_status unrolled_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   Arena a1; a1.base = (char*)wb.ptr;
   layout_all(a1, &a_csr, &y_csr, &hv, &xh, &gH, &ybar, &abar, &tmpz, &ck_y, &ck_Q, &sg_y, &sg_yc,
              &sg_d, &sg_U, &sg_V, &fin_V, &vals_in, &hvals_in, &part3);
-  SVT_CUDA(cudaMemsetAsync(W.flags, 0, 4 * sizeof(unsigned), st));
+  SVT_CUDA(cudaMemsetAsync(W.flags, 0, kFlagWords * sizeof(unsigned), st));
   SVT_CUDA(cudaMemsetAsync(A.zero_l, 0, A.zmax * sizeof(T), st));
   DeviceBlock t1, t2;
   const bool dbl_in = opt->precision == SVT_FP64;

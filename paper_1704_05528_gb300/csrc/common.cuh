@@ -79,11 +79,14 @@ __device__ __forceinline__ double block_sum(double v, double* smem32) {
 
 // ---------------------------------------------------------------- device flags
 // Bits raised by kernels into a device status word and read back by the host.
+// Words of the device status array of a solve.
+constexpr int kFlagWords = 8;
 enum : unsigned {
   FLAG_INDEX = 1u,       // index out of range in the pattern input
   FLAG_DUPLICATE = 2u,   // duplicate (row, col)
   FLAG_NONFINITE = 4u,   // non-finite value met in a reduction
   FLAG_CHOLESKY = 8u,    // non-positive pivot in a small Cholesky factorisation
+  FLAG_TC_TIMEOUT = 16u, // a bounded wait of the tensor-core lift ran out (result not written)
 };
 
 // ---------------------------------------------------------------- scratch arena

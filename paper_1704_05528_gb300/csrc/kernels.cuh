@@ -48,6 +48,21 @@ template <typename TD>
 svt_status spmm_fixup(int64_t nnz, const int32_t* ptr, const TD* part, int64_t ldp,
                       const int32_t* tails, int w, TD* out, int64_t ldo, cudaStream_t s);
 
+// lift_tc.cu ------------------------------------------------------------------
+// C (M x N, binary32, ldc) = A (M x K, binary32, lda) B (K x N, binary64, ldb) on the
+// tensor cores (three TF32 products per term).  lift_tc_fits tells whether the shape and
+// alignment are supported (K <= 128, N <= 160, 16-byte aligned A and C, leading dimensions
+// in whole 16-byte vectors); `scratch` holds lift_tc_scratch_floats() floats; a wait that
+// ran out raises FLAG_TC_TIMEOUT in *status and leaves C unwritten.
+size_t lift_tc_scratch_floats();
+// Per-device set-up (driver entry point, shared-memory limits); call it before a stream
+// capture that records lift_tc.
+svt_status lift_tc_prepare();
+bool lift_tc_fits(int64_t M, int K, int N, const float* A, int64_t lda, const float* C, int64_t ldc);
+svt_status lift_tc(int64_t M, int K, int N, const float* A, int64_t lda, const double* B,
+                   int64_t ldb, float* C, int64_t ldc, float* scratch, unsigned* status,
+                   cudaStream_t s);
+
 // dense.cu --------------------------------------------------------------------
 // C (p x q, binary64, ldc) = A^T B with A (M x p), B (M x q), reduction over M split
 // across blocks; `part` must hold gemm_tn_scratch(M, p, q) doubles.

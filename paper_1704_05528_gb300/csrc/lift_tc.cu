@@ -1,0 +1,406 @@
+// U = Q U_B on the fifth-generation tensor cores (binary32 solver path).
+//
+// The lift of the basis (Algorithm 3: U = Q U_B, Q m x r, U_B r x r) is the one dense
+// contraction of the hot path with a long dimension: m x r x r multiply-adds, about
+// 0.7 GFMA for the 71,567 x 100 workload.  Binary32 accuracy comes from three TF32 products
+// per term, A_hi B_hi + A_hi B_lo + A_lo B_hi, where x_hi is x rounded to TF32 and x_lo the
+// rounded remainder; the dropped A_lo B_lo term is below 2^-22 of |a b|.
+//
+// One CTA per SM walks 128-row tiles of Q.  The tensor memory accelerator brings each tile
+// in 32-column chunks (128-byte rows, 128-byte swizzle) into a two-stage ring; the next
+// chunk is requested as soon as the current one has landed.  The threads split a landed
+// chunk in place into its TF32 high part and a low-part copy (an elementwise operation, so
+// the swizzled layout is kept), and one thread issues the tcgen05.mma instructions
+// (M = 128, N = r rounded up to 16, K = 8 each) that accumulate the tile in tensor memory.
+// U_B^T, split the same way by a small kernel, stays in shared memory for the whole call.
+// Four warps read the accumulator back with tcgen05.ld and store the tile.
+//
+// Every wait is bounded: a wait that runs out raises FLAG_TC_TIMEOUT in the status word,
+// the CTA stops issuing work, waits (bounded) for what it issued and releases its tensor
+// memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace svt {
+namespace {
+
+constexpr int kBM = 128;        // rows per tile: one tensor-memory lane per row
+constexpr int kKC = 32;         // K columns per chunk: 128 bytes of binary32
+constexpr int kMaxChunks = 4;   // K <= 128
+constexpr int kThreads = 256;
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase of the given parity; false when it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t spin = 0; spin < kSpinLimit; ++spin) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor of a K-major operand with 128-byte swizzle: rows of 128
+// bytes, groups of eight rows 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  uint64_t d = (saddr(p) & 0x3FFFFu) >> 4;  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused by this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: D binary32, A and B TF32, both K-major, M x N.
+constexpr uint32_t instr_desc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
+}
+
+template <int NPAD>
+struct Layout {
+  static constexpr int kBChunk = NPAD * 128;           // bytes of one K chunk of U_B^T
+  static constexpr int kB = 2 * kMaxChunks * kBChunk;  // high and low parts
+  static constexpr int kAChunk = kBM * 128;            // 16 KB
+  static constexpr int kA = 2 * 2 * kAChunk;           // two stages of (high, low)
+  static constexpr int kBar = 64;
+  static constexpr int bytes = kB + kA + kBar + 1024;  // + 1024-byte alignment slack
+  static constexpr int tmem_cols = NPAD <= 32 ? 32 : NPAD <= 64 ? 64 : NPAD <= 128 ? 128 : 256;
+};
+
+template <int NPAD>
+__global__ void __launch_bounds__(kThreads, 1)
+k_lift_tf32x3(int M, int N, int K, const __grid_constant__ CUtensorMap mapA,
+              const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
+              float* __restrict__ C, int64_t ldc, unsigned* __restrict__ status) {
+  using L = Layout<NPAD>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + L::kB;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::kB + L::kA);
+  uint64_t* barB = bar + 0;
+  uint64_t* barFull = bar + 1;  // [2] a chunk has landed in the stage
+  uint64_t* barFree = bar + 3;  // [2] the MMAs that read the stage have completed
+  uint64_t* barAcc = bar + 5;   // the tile's accumulator is complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 6);
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nchunks = (K + kKC - 1) / kKC;
+  const int ntiles = (M + kBM - 1) / kBM;
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(barB, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(barFull + s, 1);
+      mbar_init(barFree + s, 1);
+    }
+    mbar_init(barAcc, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(tmem_slot)),
+                 "r"((uint32_t)L::tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  // chunk sequence of this CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ..., each in
+  // nchunks chunks; chunk j goes to stage j & 1
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int total = my_tiles * nchunks;
+  bool issued[2] = {false, false};
+  uint32_t free_phase[2] = {0, 0};
+  auto issue = [&](int j) {  // thread 0: request chunk j into its stage
+    const int s = j & 1;
+    if (issued[s]) {  // the MMAs of chunk j - 2 read this stage
+      if (!mbar_wait(barFree + s, free_phase[s])) { s_abort = 1; return; }
+      free_phase[s] ^= 1;
+    }
+    const int tile = blockIdx.x + (j / nchunks) * gridDim.x, c = j % nchunks;
+    mbar_expect_tx(barFull + s, (uint32_t)L::kAChunk);
+    tma_load_2d(sA + s * 2 * L::kAChunk, &mapA, c * kKC, tile * kBM, barFull + s);
+    issued[s] = true;
+  };
+  if (tid == 0) {
+    mbar_expect_tx(barB, (uint32_t)(2 * nchunks * L::kBChunk));
+    for (int c = 0; c < nchunks; ++c) {
+      tma_load_2d(sB + c * L::kBChunk, &mapBhi, c * kKC, 0, barB);
+      tma_load_2d(sB + (kMaxChunks + c) * L::kBChunk, &mapBlo, c * kKC, 0, barB);
+    }
+    if (total > 0) issue(0);
+  }
+  if (!mbar_wait(barB, 0)) s_abort = 1;
+  const uint32_t idesc = instr_desc_tf32(kBM, NPAD);
+  uint32_t full_phase[2] = {0, 0}, acc_phase = 0;
+  int j = 0;
+  for (int t = 0; t < my_tiles; ++t) {
+    const int tile = blockIdx.x + t * gridDim.x;
+    for (int c = 0; c < nchunks; ++c, ++j) {
+      const int s = j & 1;
+      unsigned char* a_hi = sA + s * 2 * L::kAChunk;
+      unsigned char* a_lo = a_hi + L::kAChunk;
+      __syncthreads();
+      if (s_abort) break;
+      if (!mbar_wait(barFull + s, full_phase[s])) s_abort = 1;
+      full_phase[s] ^= 1;
+      __syncthreads();
+      if (s_abort) break;
+      if (tid == 0 && j + 1 < total) issue(j + 1);  // overlaps this chunk's split and MMAs
+      float4* hi4 = reinterpret_cast<float4*>(a_hi);
+      float4* lo4 = reinterpret_cast<float4*>(a_lo);
+      for (int i = tid; i < L::kAChunk / 16; i += kThreads) {
+        const float4 x = hi4[i];
+        float4 h;
+        h.x = tf32_round(x.x); h.y = tf32_round(x.y); h.z = tf32_round(x.z); h.w = tf32_round(x.w);
+        hi4[i] = h;
+        lo4[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+      __syncthreads();
+      if (tid == 0 && !s_abort) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned char* b_hi = sB + c * L::kBChunk;
+        const unsigned char* b_lo = sB + (kMaxChunks + c) * L::kBChunk;
+#pragma unroll
+        for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per instruction: 32 bytes along the row
+          const uint64_t ah = smem_desc(a_hi + kk * 32), al = smem_desc(a_lo + kk * 32);
+          const uint64_t bh = smem_desc(b_hi + kk * 32), bl = smem_desc(b_lo + kk * 32);
+          mma_tf32(tmem, ah, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+          mma_tf32(tmem, ah, bl, idesc, 1u);
+          mma_tf32(tmem, al, bh, idesc, 1u);
+        }
+        mma_commit(barFree + s);
+        if (c == nchunks - 1) mma_commit(barAcc);
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (!mbar_wait(barAcc, acc_phase)) s_abort = 1;
+    acc_phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp < 4 && !s_abort) {  // warp w reads tensor-memory lanes 32w .. 32w + 31
+      const int64_t row = (int64_t)tile * kBM + warp * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < NPAD; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < M) {
+          float* dst = C + row * ldc + c0;
+          if (c0 + 16 <= N) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              reinterpret_cast<float4*>(dst)[q] =
+                  make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (c0 + q < N) dst[q] = __uint_as_float(v[q]);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (s_abort) {
+      atomicOr(status, FLAG_TC_TIMEOUT);
+      // nothing issued may still write shared or tensor memory: bounded waits for the
+      // last MMA commit of each stage
+      for (int s = 0; s < 2; ++s)
+        if (issued[s]) mbar_wait(barFree + s, free_phase[s]);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)L::tmem_cols)
+                 : "memory");
+  }
+}
+
+// Bt_hi, Bt_lo (npad x 128, K-major) = TF32 parts of (binary32) B^T for B (K x N, binary64,
+// row-major, ldb); zero outside K x N.
+__global__ void k_split_bt(int K, int N, int npad, const double* __restrict__ B, int64_t ldb,
+                           float* __restrict__ bhi, float* __restrict__ blo) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npad * 128) return;
+  const int n = t / 128, k = t % 128;
+  float h = 0.f, l = 0.f;
+  if (n < N && k < K) {
+    const float b = (float)B[(int64_t)k * ldb + n];
+    h = tf32_round(b);
+    l = b - h;
+  }
+  bhi[t] = h;
+  blo[t] = l;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* map, const float* base, uint64_t inner, uint64_t outer,
+               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t gstr[1] = {(cuuint64_t)row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NPAD>
+cudaError_t set_smem_limit() {
+  return cudaFuncSetAttribute(k_lift_tf32x3<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Layout<NPAD>::bytes);
+}
+
+// shared-memory limits of every instantiation, once per device
+std::mutex g_prep_mu;
+uint64_t g_prep_devices = 0;
+
+template <int NPAD>
+svt_status launch_lift(int64_t M, int K, int N, const CUtensorMap& mA, const CUtensorMap& mBh,
+                       const CUtensorMap& mBl, float* C, int64_t ldc, unsigned* status,
+                       cudaStream_t s) {
+  using L = Layout<NPAD>;
+  const int64_t ntiles = ceil_div(M, (int64_t)kBM);
+  const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
+  k_lift_tf32x3<NPAD><<<grid, kThreads, L::bytes, s>>>((int)M, N, K, mA, mBh, mBl, C, ldc, status);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+}  // namespace
+
+// N rounded up to a tile width with an instantiated kernel (shared memory holds U_B^T
+// for up to 160 columns next to the two-stage ring)
+int lift_npad(int N) { return N <= 128 ? (int)round_up(N, 16) : N <= 144 ? 144 : 160; }
+
+size_t lift_tc_scratch_floats() { return (size_t)2 * 160 * 128; }
+
+svt_status lift_tc_prepare() {
+  int dev = 0;
+  SVT_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_prep_mu);
+  const uint64_t bit = 1ull << (dev & 63);
+  if (g_prep_devices & bit) return SVT_OK;
+  if (!encode_fn()) return fail(SVT_ERR_UNSUPPORTED, "tensor-core lift: no tensor map encoder");
+  SVT_CUDA(set_smem_limit<16>()); SVT_CUDA(set_smem_limit<32>()); SVT_CUDA(set_smem_limit<48>());
+  SVT_CUDA(set_smem_limit<64>()); SVT_CUDA(set_smem_limit<80>()); SVT_CUDA(set_smem_limit<96>());
+  SVT_CUDA(set_smem_limit<112>()); SVT_CUDA(set_smem_limit<128>()); SVT_CUDA(set_smem_limit<144>());
+  SVT_CUDA(set_smem_limit<160>());
+  g_prep_devices |= bit;
+  return SVT_OK;
+}
+
+bool lift_tc_fits(int64_t M, int K, int N, const float* A, int64_t lda, const float* C, int64_t ldc) {
+  return M > 0 && M < (int64_t)INT32_MAX - kBM && K >= 1 && K <= kMaxChunks * kKC && N >= 1 &&
+         N <= 160 && lda % 4 == 0 && ldc % 4 == 0 && lda >= K && ldc >= N &&
+         reinterpret_cast<uintptr_t>(A) % 16 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0 &&
+         encode_fn() != nullptr;
+}
+
+svt_status lift_tc(int64_t M, int K, int N, const float* A, int64_t lda, const double* B,
+                   int64_t ldb, float* C, int64_t ldc, float* scratch, unsigned* status,
+                   cudaStream_t s) {
+  if (!lift_tc_fits(M, K, N, A, lda, C, ldc))
+    return fail(SVT_ERR_UNSUPPORTED, "tensor-core lift: unsupported shape or alignment");
+  SVT_TRY(lift_tc_prepare());
+  const int npad = lift_npad(N);
+  float* bhi = scratch;
+  float* blo = scratch + (size_t)npad * 128;
+  k_split_bt<<<(int)ceil_div((int64_t)npad * 128, 256), 256, 0, s>>>(K, N, npad, B, ldb, bhi, blo);
+  SVT_LAUNCH_CHECK();
+  CUtensorMap mA, mBh, mBl;
+  if (!encode_2d(&mA, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda * 4, kKC, kBM) ||
+      !encode_2d(&mBh, bhi, 128, (uint64_t)npad, 128 * 4, kKC, (uint32_t)npad) ||
+      !encode_2d(&mBl, blo, 128, (uint64_t)npad, 128 * 4, kKC, (uint32_t)npad))
+    return fail(SVT_ERR_CUDA, "tensor-core lift: tensor map encoding failed");
+#define SVT_LIFT(NP) \
+  case NP: return launch_lift<NP>(M, K, N, mA, mBh, mBl, C, ldc, status, s)
+  switch (npad) {
+    SVT_LIFT(16); SVT_LIFT(32); SVT_LIFT(48); SVT_LIFT(64); SVT_LIFT(80); SVT_LIFT(96);
+    SVT_LIFT(112); SVT_LIFT(128); SVT_LIFT(144); SVT_LIFT(160);
+    default: break;
+  }
+#undef SVT_LIFT
+  return fail(SVT_ERR_UNSUPPORTED, "tensor-core lift: N = %d", N);
+}
+
+}  // namespace svt

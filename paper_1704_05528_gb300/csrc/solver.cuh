@@ -263,7 +263,10 @@ struct Work {
   double *Gx = nullptr, *Rm = nullptr, *Rinv = nullptr, *cwork = nullptr, *Tsm = nullptr;
   double *coef = nullptr, *part = nullptr, *eigw = nullptr, *dsc = nullptr, *colss = nullptr;
   double *pv = nullptr, *pu = nullptr, *pw = nullptr;  // power-iteration vectors
+  // status words: [0] FLAG bits, [1] cluster-start status, [2] Jacobi sweeps, [3] check
+  // status, [4] sticky FLAG_TC_TIMEOUT of the tensor-core lift
   unsigned* flags = nullptr;
+  float* tcb = nullptr;             // split U_B^T for the tensor-core lift (binary32 path)
   void* spmm_scr = nullptr;         // partial rows of the entry-chunked SpMM
   // Set by a caller whose sampled update already formed Bt = Y^T Q for the s recycled
   // columns (the fused update); r4svd_run then skips that product and clears it.
@@ -284,7 +287,7 @@ struct Work {
     cudaStream_t s = nullptr;
     ~OwnedStream() { if (s) cudaStreamDestroy(s); }
   } cap;
-  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + 8; }
+  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + kFlagWords; }
 
   void layout(Arena& a) {
     const int64_t m = P.m, n = P.n, z = pat->nnz;
@@ -317,7 +320,8 @@ struct Work {
     dsc = a.take<double>(16);
     colss = a.take<double>(std::max(wmax, rc));
     pv = a.take<double>(n); pw = a.take<double>(n); pu = a.take<double>(m);
-    flags = a.take<unsigned>(4);
+    flags = a.take<unsigned>(kFlagWords);
+    if (sizeof(T) == 4) tcb = a.take<float>(lift_tc_scratch_floats());
     const size_t sb = std::max(spmm_scratch_bytes(z, std::max(wmax, rc), (int)sizeof(T)),
                                spmm_scratch_bytes(z, 1, 8));
     spmm_scr = a.take<char>(sb);
@@ -357,6 +361,16 @@ struct R4Out {
 // Algorithm 3 (Algorithm 2 when s == 0).  Q holds the recycled basis in columns [0, s);
 // new blocks are appended in place.  On return U = Q U_B is written to Unew (m x ldq),
 // Bt (n x r) = Y^T Q, W.Ub = U_B, sigma on the host.
+// U = Q U_B (m x r times r x r, Algorithm 3): on the tensor cores in the binary32 path
+template <typename T>
+svt_status lift_basis(Work<T>& W, const T* Q, int r, T* Unew) {
+  if constexpr (sizeof(T) == 4) {
+    if (W.tcb && lift_tc_fits(W.P.m, r, r, Q, W.ldq, Unew, W.ldq))
+      return lift_tc(W.P.m, r, r, Q, W.ldq, W.Ub, r, Unew, W.ldq, W.tcb, W.flags + 4, W.s);
+  }
+  return gemm_nn<T, T>(W.P.m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, W.s);
+}
+
 enum class EigFrom {
   kClusters,  // near-diagonal cluster start, checked refinement, second pass, else Jacobi
   kRejected,  // the checked refinement from the cluster start was refused: second pass
@@ -426,9 +440,12 @@ svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram,
   // U = Q U_B (all r columns are recycled)
   {
     SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
-    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+    SVT_TRY(lift_basis<T>(W, Q, r, Unew));
   }
+  unsigned tc_status = 0;
+  SVT_CUDA(cudaMemcpyAsync(&tc_status, W.flags + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   SVT_CUDA(cudaStreamSynchronize(st));
+  if (tc_status & FLAG_TC_TIMEOUT) return fail(SVT_ERR_CUDA, "tensor-core lift: a bounded wait ran out");
   prof_flush();
   if (g_prof_on && !near_diagonal) {  // sweep count of the binary32 Jacobi stage (pseudo-entry)
     int sweeps = 0;
@@ -473,10 +490,10 @@ svt_status eig_phase_enqueue(Work<T>& W, T* Q, int r, T* Unew) {
                        reinterpret_cast<int*>(W.flags + 3), near_diagonal_tol<T>()));
   }
   SVT_CUDA(cudaMemcpyAsync(W.host_pin + r, W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SVT_CUDA(cudaMemcpyAsync(W.host_pin + 2 * r, W.flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  SVT_CUDA(cudaMemcpyAsync(W.host_pin + 2 * r, W.flags, kFlagWords * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   {
     SVT_PROF("lift_U", gemm_bytes(m, r, r, sv, false), st);
-    SVT_TRY((gemm_nn<T, T>(m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, st)));
+    SVT_TRY(lift_basis<T>(W, Q, r, Unew));
   }
   return SVT_OK;
 }
@@ -496,6 +513,7 @@ svt_status eig_phase_graph(Work<T>& W, T* Q, int r, T* Unew, bool* ran) {
     g = W.eg[0].used <= W.eg[1].used ? &W.eg[0] : &W.eg[1];
     g->reset();
     SVT_TRY(eig_prepare());
+    if (sizeof(T) == 4) SVT_TRY(lift_tc_prepare());
     if (!W.cap.s) SVT_CUDA(cudaStreamCreateWithFlags(&W.cap.s, cudaStreamNonBlocking));
     std::vector<Pending> scopes;
     const int64_t l0 = launches_so_far();
@@ -564,8 +582,9 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
       for (int c = 0; c < s; ++c) normB += hp[c];
       const double eps0 = eps_of(normB);
       if (!(eps0 > eps_thr && s < P.r_cap)) {  // no new block: the graph's results stand
-        unsigned fl[4];
+        unsigned fl[kFlagWords];
         memcpy(fl, hp + 2 * s, sizeof(fl));
+        if (fl[4] & FLAG_TC_TIMEOUT) return fail(SVT_ERR_CUDA, "tensor-core lift: a bounded wait ran out");
         o->r = s; o->blocks = 0; o->exhausted = false; o->eps = eps0; o->normB = normB;
         o->sigma.assign(s, 0.0);
         if (fl[1] == 0 && fl[3] == 0) {

@@ -206,7 +206,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   Arena b; b.base = (char*)wblk.ptr;
   take_own(b, &a_csr, &y_csr, &a_csc, &bt_alt, &fpart);
   W.layout(b);
-  SVT_CUDA(cudaMemsetAsync(W.flags, 0, 4 * sizeof(unsigned), st));
+  SVT_CUDA(cudaMemsetAsync(W.flags, 0, kFlagWords * sizeof(unsigned), st));
 
   // P_Lambda(A) in CSR order; reject non-finite values.
   SVT_TRY((gather_convert<T, T>(nnz, pat->csr_src, d_vals, a_csr, st)));
@@ -374,7 +374,7 @@ svt_status r4svd_impl(const svt_pattern* p, const T* y_csr, const T* U_prev, int
   SVT_TRY(blk.alloc(a.off, st));
   Arena b; b.base = (char*)blk.ptr;
   W.layout(b);
-  SVT_CUDA(cudaMemsetAsync(W.flags, 0, 4 * sizeof(unsigned), st));
+  SVT_CUDA(cudaMemsetAsync(W.flags, 0, kFlagWords * sizeof(unsigned), st));
   const int64_t nnz = p->nnz;
   SVT_TRY(launch_gather<T>(nnz, p->perm, y_csr, W.y_csc, st));
   double normY2 = 0.0;
