@@ -287,6 +287,32 @@ def test_r4svd_parity(svt, torch_mod, eps_thr, n_power):
     assert _rel(Xg, Xo) < FP64_TOL
 
 
+@pytest.mark.parametrize("r_max", [100, 128, 16, 40, 150])
+def test_r4svd_mixed_lift(svt, torch_mod, r_max):
+    """Binary32 R4SVD: U = Q U_B runs on the tensor cores (three TF32 products per term)
+    for r <= 128 and on the binary32 SIMT kernel above that.  1,000 rows span eight
+    128-row tiles and a ragged tail; the basis must stay orthonormal and the well-separated
+    rank-10 part must match the binary64 oracle."""
+    w = workloads.random_lowrank(1000, 300, 10, 0.3, seed=21)
+    ref_p = oracle.build_pattern(w.m, w.n, w.rows, w.cols)
+    P = svt.Pattern(w.m, w.n, w.rows, w.cols)
+    y = w.vals[ref_p.csr_src] * 12.0
+    Ys = OF._sparse(ref_p, y)
+    kw = dict(t=min(r_max, 30), dt=10, n_power=0)
+    ro = oracle.r4svd(Ys, None, 1e-12, 1, r_cap=r_max, seed=w.seed, **kw)
+    rg = svt.r4svd(P, torch_mod.from_numpy(y), 1e-12, 1, seed=w.seed, r_max=r_max,
+                   precision="mixed", **kw)
+    assert rg["r"] == ro.r == r_max
+    U = rg["U"].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(U.T @ U - np.eye(r_max))) < 2e-5
+    S = rg["S"].cpu().numpy()
+    k = 10
+    assert np.max(np.abs(S[:k] - ro.S[:k])) / ro.S[0] < 1e-5
+    Xo = (ro.U[:, :k] * ro.S[:k]) @ ro.V[:, :k].T
+    Xg = (U[:, :k] * S[:k]) @ rg["V"][:, :k].cpu().numpy().astype(np.float64).T
+    assert _rel(Xg, Xo) < 1e-4
+
+
 def _oracle_state(w, it_stop, **kw):
     """(Y in CSR order at SVT iteration it_stop, the basis that iteration recycles), from
     the oracle's own solve."""
