@@ -222,10 +222,14 @@ k_update_recycle(int32_t n, int32_t nnz, int32_t C, int32_t nchunks,
                  T* __restrict__ slots, int64_t ldp, int32_t* __restrict__ tail_col,
                  double* __restrict__ part, unsigned* __restrict__ flags) {
   constexpr int NG = 32 / G;
-  const int lane = threadIdx.x & 31;
+  __shared__ double s_wpart[8][3];
+  __shared__ unsigned s_done;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane % G;
   // entry offsets fit in int32: the pattern's column pointers are int32
   const int32_t chunk = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (threadIdx.x == 0) s_done = 0;
+  __syncthreads();
   SumAcc<T> acc_d2, acc_abs, acc_y2;
   bool bad = false;
   if (chunk < nchunks) {  // warp-uniform
@@ -345,17 +349,28 @@ k_update_recycle(int32_t n, int32_t nnz, int32_t C, int32_t nchunks,
     if (lane == 0) tail_col[chunk] = my_tail;
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NONFINITE);
-  // one partial per chunk (fixed shuffle tree), summed in chunk order by k_finish; no
-  // block-wide barrier, so a warp leaves as soon as its chunk is done
-  if (chunk < nchunks) {
-    const double s_d2 = warp_sum(acc_d2.value());
-    const double s_abs = warp_sum(acc_abs.value());
-    const double s_y2 = warp_sum(acc_y2.value());
-    if (lane == 0) {
-      part[(int64_t)chunk * 3 + 0] = s_d2;
-      part[(int64_t)chunk * 3 + 1] = s_abs;
-      part[(int64_t)chunk * 3 + 2] = s_y2;
-    }
+  // One partial per block, summed in block order by k_finish.  Each warp's sums (fixed
+  // shuffle tree) go to shared memory, and the last warp of the block to finish adds them
+  // in warp order: there is no block-wide barrier, so a warp leaves as soon as its chunk
+  // is done.
+  const double s_d2 = warp_sum(acc_d2.value());
+  const double s_abs = warp_sum(acc_abs.value());
+  const double s_y2 = warp_sum(acc_y2.value());
+  unsigned last = 0;
+  if (lane == 0) {
+    s_wpart[warp][0] = s_d2;
+    s_wpart[warp][1] = s_abs;
+    s_wpart[warp][2] = s_y2;
+    __threadfence_block();
+    last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1 ? 1u : 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last && lane < 3) {
+    __threadfence_block();
+    const volatile double* wp = &s_wpart[0][0];
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wp[w * 3 + lane];
+    part[(int64_t)blockIdx.x * 3 + lane] = t;
   }
 }
 
@@ -498,7 +513,7 @@ svt_status sampled_update(const svt_pattern* p, const T* U, int64_t ldu, const T
 
 namespace {
 
-int64_t recycle_chunks(int64_t nnz) { return ceil_div(nnz, chunk_size(nnz)); }
+int64_t recycle_blocks(int64_t nnz) { return ceil_div(ceil_div(nnz, chunk_size(nnz)), 8); }
 
 template <typename T, int VEC, int G, int MAXV, int UNR, int MINB>
 svt_status run_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, const T* W,
@@ -511,7 +526,7 @@ svt_status run_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, con
   int64_t ldp;
   int32_t* tails;
   spmm_slots<T>(scratch, z, r, &slots, &ldp, &tails);
-  k_update_recycle<T, VEC, G, MAXV, UNR, MINB><<<(int)ceil_div(nchunks, 8), 256, 0, s>>>(
+  k_update_recycle<T, VEC, G, MAXV, UNR, MINB><<<(int)recycle_blocks(z), 256, 0, s>>>(
       (int32_t)p->n, (int32_t)z, (int32_t)C, (int32_t)nchunks, p->col_ptr, p->row_idx, p->chunk_row_csc, U, ldu, r, W, ldw, k, a, y,
       (T)delta, bt, ldb, slots, ldp, tails, part, flags);
   SVT_LAUNCH_CHECK();
@@ -548,7 +563,7 @@ bool update_recycle_fits(int r, int64_t nnz) {
 }
 
 size_t update_recycle_scratch(int64_t nnz) {
-  return (size_t)(3 * recycle_chunks(nnz > 0 ? nnz : 1) + 8);
+  return (size_t)(3 * recycle_blocks(nnz > 0 ? nnz : 1) + 8);
 }
 
 template <typename T>
@@ -569,7 +584,7 @@ svt_status update_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, 
   }
   SVT_TRY((dispatch_recycle<T, V>(p, U, ldu, r, W, ldw, k, a, y, delta, bt, ldb, part, flags,
                                    scratch, s)));
-  k_finish<<<3, 256, 0, s>>>((int)recycle_chunks(p->nnz), 3, 3, part, out3);
+  k_finish<<<3, 256, 0, s>>>((int)recycle_blocks(p->nnz), 3, 3, part, out3);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }

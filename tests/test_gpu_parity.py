@@ -416,6 +416,19 @@ def _assert_fp64_parity(w, ref, got):
         assert np.max(np.abs(s_got - ref.S) / (ref.S + w.tau)) < FP64_TOL
 
 
+def test_complete_fp64_above_fused_rank(svt, torch_mod):
+    """Revealed rank above the fused update's binary64 limit (256 columns): the solver
+    switches to the CSR-order sampled update, keeps the CSC copy of Y by regathering it,
+    and refreshes the CSR copy when the fused pass wrote only the CSC one."""
+    w = workloads.random_lowrank(420, 380, 6, 0.5, seed=17, maxit=8, tol=1e-12)
+    w.tau = np.sqrt(w.m * w.n)  # keeps the separated rank-6 part (k = 5-6)
+    ref, got = _run_pair(svt, torch_mod, w, w.maxit, "fp64", t=240, dt=12, r_max=300,
+                         eps_thr0=0.05)
+    rs = [e["r"] for e in ref.log]
+    assert min(rs) <= 256 < max(rs), rs  # both the fused and the CSR-order update ran
+    _assert_fp64_parity(w, ref, got)
+
+
 def test_complete_fp64_lowrank500(svt, torch_mod):
     """500x500 rank-10, 20% observed: the full 200-iteration run."""
     w = workloads.small_lowrank()
