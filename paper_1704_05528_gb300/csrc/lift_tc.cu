@@ -6,14 +6,14 @@
 // per term, A_hi B_hi + A_hi B_lo + A_lo B_hi, where x_hi is x rounded to TF32 and x_lo the
 // rounded remainder; the dropped A_lo B_lo term is below 2^-22 of |a b|.
 //
-// One CTA per SM walks 128-row tiles of Q.  The tensor memory accelerator brings each tile
-// in 32-column chunks (128-byte rows, 128-byte swizzle) into a two-stage ring; the next
-// chunk is requested as soon as the current one has landed.  The threads split a landed
-// chunk in place into its TF32 high part and a low-part copy (an elementwise operation, so
-// the swizzled layout is kept), and one thread issues the tcgen05.mma instructions
-// (M = 128, N = r rounded up to 16, K = 8 each) that accumulate the tile in tensor memory.
+// One CTA per SM walks 128-row tiles of Q with warp-specialised stages.  The tensor memory
+// accelerator brings each tile in 32-column chunks (128-byte rows, 128-byte swizzle) into
+// a ring of two or three stages.  Two warps split a landed chunk in place into its TF32
+// high part and a low-part copy (an elementwise operation, so the swizzled layout is
+// kept); one thread issues the tcgen05.mma instructions (M = 128, N = r rounded up to 16,
+// K = 8 each) that accumulate the tile in one of two tensor-memory accumulators; four
+// warps read the other accumulator back with tcgen05.ld and store the previous tile.
 // U_B^T, split the same way by a small kernel, stays in shared memory for the whole call.
-// Four warps read the accumulator back with tcgen05.ld and store the tile.
 //
 // Every wait is bounded: a wait that runs out raises FLAG_TC_TIMEOUT in the status word,
 // the CTA stops issuing work, waits (bounded) for what it issued and releases its tensor
@@ -102,49 +102,72 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(h);
 }
 
+// Stages of the A ring: as many 32 KB stages (high and low part of a 128 x 32 chunk) as
+// fit next to U_B^T.
 template <int NPAD>
 struct Layout {
   static constexpr int kBChunk = NPAD * 128;           // bytes of one K chunk of U_B^T
   static constexpr int kB = 2 * kMaxChunks * kBChunk;  // high and low parts
   static constexpr int kAChunk = kBM * 128;            // 16 KB
-  static constexpr int kA = 2 * 2 * kAChunk;           // two stages of (high, low)
-  static constexpr int kBar = 64;
+  static constexpr int kStages = (kB + 3 * 2 * kAChunk + 2048 <= 232448) ? 3 : 2;
+  static constexpr int kA = kStages * 2 * kAChunk;
+  static constexpr int kBar = 256;
   static constexpr int bytes = kB + kA + kBar + 1024;  // + 1024-byte alignment slack
-  static constexpr int tmem_cols = NPAD <= 32 ? 32 : NPAD <= 64 ? 64 : NPAD <= 128 ? 128 : 256;
+  // two accumulators (tile t in buffer t & 1) 32-column aligned, in a power of two of
+  // tensor-memory columns
+  static constexpr int kAccStride = (NPAD + 31) / 32 * 32;
+  static constexpr int kCols = kAccStride + NPAD;
+  static constexpr int tmem_cols = kCols <= 32 ? 32 : kCols <= 64 ? 64 : kCols <= 128 ? 128 : kCols <= 256 ? 256 : 512;
 };
 
+// Warp roles: warp 0 requests chunks of A (TMA), warps 2-3 split them into TF32 parts,
+// warp 1 issues the MMAs, warps 4-7 read the accumulators back (warp 4 + i owns tensor
+// memory lanes 32i .. 32i + 31) and store the tiles.  Tiles alternate between two
+// accumulators, so the store of tile t overlaps the MMAs of tile t + 1.
 template <int NPAD>
 __global__ void __launch_bounds__(kThreads, 1)
 k_lift_tf32x3(int M, int N, int K, const __grid_constant__ CUtensorMap mapA,
               const __grid_constant__ CUtensorMap mapBhi, const __grid_constant__ CUtensorMap mapBlo,
               float* __restrict__ C, int64_t ldc, unsigned* __restrict__ status) {
   using L = Layout<NPAD>;
+  constexpr int S = L::kStages;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sB = smem;
   unsigned char* sA = smem + L::kB;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::kB + L::kA);
-  uint64_t* barB = bar + 0;
-  uint64_t* barFull = bar + 1;  // [2] a chunk has landed in the stage
-  uint64_t* barFree = bar + 3;  // [2] the MMAs that read the stage have completed
-  uint64_t* barAcc = bar + 5;   // the tile's accumulator is complete
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 6);
+  uint64_t* barB = bar;                  // U_B^T has landed
+  uint64_t* barFull = bar + 1;           // [S] a chunk of A has landed
+  uint64_t* barSplit = barFull + S;      // [S] the chunk is split (two arrivals)
+  uint64_t* barEmpty = barSplit + S;     // [S] the MMAs that read the stage have completed
+  uint64_t* barAccFull = barEmpty + S;   // [2] an accumulator holds a finished tile
+  uint64_t* barAccEmpty = barAccFull + 2;  // [2] its tile has been stored (128 arrivals)
+  uint64_t* barDrain = barAccEmpty + 2;    // every MMA issued so far has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barDrain + 1);
   __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nchunks = (K + kKC - 1) / kKC;
   const int ntiles = (M + kBM - 1) / kBM;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int total = my_tiles * nchunks;
   if (tid == 0) {
     s_abort = 0;
     mbar_init(barB, 1);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(barFull + s, 1);
-      mbar_init(barFree + s, 1);
+      mbar_init(barSplit + s, 64);
+      mbar_init(barEmpty + s, 1);
     }
-    mbar_init(barAcc, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(barAccFull + b, 1);
+      mbar_init(barAccEmpty + b, 128);
+    }
+    mbar_init(barDrain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      saddr(tmem_slot)),
                  "r"((uint32_t)L::tmem_cols)
@@ -155,51 +178,38 @@ k_lift_tf32x3(int M, int N, int K, const __grid_constant__ CUtensorMap mapA,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  // chunk sequence of this CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ..., each in
-  // nchunks chunks; chunk j goes to stage j & 1
-  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int total = my_tiles * nchunks;
-  bool issued[2] = {false, false};
-  uint32_t free_phase[2] = {0, 0};
-  auto issue = [&](int j) {  // thread 0: request chunk j into its stage
-    const int s = j & 1;
-    if (issued[s]) {  // the MMAs of chunk j - 2 read this stage
-      if (!mbar_wait(barFree + s, free_phase[s])) { s_abort = 1; return; }
-      free_phase[s] ^= 1;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      mbar_expect_tx(barB, (uint32_t)(2 * nchunks * L::kBChunk));
+      for (int c = 0; c < nchunks; ++c) {
+        tma_load_2d(sB + c * L::kBChunk, &mapBhi, c * kKC, 0, barB);
+        tma_load_2d(sB + (kMaxChunks + c) * L::kBChunk, &mapBlo, c * kKC, 0, barB);
+      }
+      int issued = 0;
+      for (int j = 0; j < total && !*abort_flag; ++j) {
+        const int s = j % S;
+        if (j >= S && !mbar_wait(barEmpty + s, (uint32_t)((j / S - 1) & 1))) { *abort_flag = 1; break; }
+        const int tile = blockIdx.x + (j / nchunks) * gridDim.x, c = j % nchunks;
+        mbar_expect_tx(barFull + s, (uint32_t)L::kAChunk);
+        tma_load_2d(sA + s * 2 * L::kAChunk, &mapA, c * kKC, tile * kBM, barFull + s);
+        issued = j + 1;
+      }
+      // after a failure nothing may still land in shared memory when the CTA leaves:
+      // bounded waits for the last load of each stage
+      if (*abort_flag)
+        for (int j = issued - S > 0 ? issued - S : 0; j < issued; ++j)
+          mbar_wait(barFull + j % S, (uint32_t)((j / S) & 1));
     }
-    const int tile = blockIdx.x + (j / nchunks) * gridDim.x, c = j % nchunks;
-    mbar_expect_tx(barFull + s, (uint32_t)L::kAChunk);
-    tma_load_2d(sA + s * 2 * L::kAChunk, &mapA, c * kKC, tile * kBM, barFull + s);
-    issued[s] = true;
-  };
-  if (tid == 0) {
-    mbar_expect_tx(barB, (uint32_t)(2 * nchunks * L::kBChunk));
-    for (int c = 0; c < nchunks; ++c) {
-      tma_load_2d(sB + c * L::kBChunk, &mapBhi, c * kKC, 0, barB);
-      tma_load_2d(sB + (kMaxChunks + c) * L::kBChunk, &mapBlo, c * kKC, 0, barB);
-    }
-    if (total > 0) issue(0);
-  }
-  if (!mbar_wait(barB, 0)) s_abort = 1;
-  const uint32_t idesc = instr_desc_tf32(kBM, NPAD);
-  uint32_t full_phase[2] = {0, 0}, acc_phase = 0;
-  int j = 0;
-  for (int t = 0; t < my_tiles; ++t) {
-    const int tile = blockIdx.x + t * gridDim.x;
-    for (int c = 0; c < nchunks; ++c, ++j) {
-      const int s = j & 1;
-      unsigned char* a_hi = sA + s * 2 * L::kAChunk;
-      unsigned char* a_lo = a_hi + L::kAChunk;
-      __syncthreads();
-      if (s_abort) break;
-      if (!mbar_wait(barFull + s, full_phase[s])) s_abort = 1;
-      full_phase[s] ^= 1;
-      __syncthreads();
-      if (s_abort) break;
-      if (tid == 0 && j + 1 < total) issue(j + 1);  // overlaps this chunk's split and MMAs
-      float4* hi4 = reinterpret_cast<float4*>(a_hi);
-      float4* lo4 = reinterpret_cast<float4*>(a_lo);
-      for (int i = tid; i < L::kAChunk / 16; i += kThreads) {
+  } else if (warp == 2 || warp == 3) {  // split: 64 threads per chunk
+    const int t64 = tid - 64;
+    for (int j = 0; j < total && !*abort_flag; ++j) {
+      const int s = j % S;
+      if (!mbar_wait(barFull + s, (uint32_t)((j / S) & 1))) { *abort_flag = 1; break; }
+      float4* hi4 = reinterpret_cast<float4*>(sA + s * 2 * L::kAChunk);
+      float4* lo4 = reinterpret_cast<float4*>(sA + s * 2 * L::kAChunk + L::kAChunk);
+#pragma unroll 4
+      for (int i = t64; i < L::kAChunk / 16; i += 64) {
         const float4 x = hi4[i];
         float4 h;
         h.x = tf32_round(x.x); h.y = tf32_round(x.y); h.z = tf32_round(x.z); h.w = tf32_round(x.w);
@@ -207,34 +217,51 @@ k_lift_tf32x3(int M, int N, int K, const __grid_constant__ CUtensorMap mapA,
         lo4[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
-      __syncthreads();
-      if (tid == 0 && !s_abort) {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(barSplit + s)) : "memory");
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = instr_desc_tf32(kBM, NPAD);
+      if (!mbar_wait(barB, 0)) *abort_flag = 1;
+      int j = 0;
+      for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
+        const int b = t & 1;
+        const uint32_t acc = tmem + (uint32_t)(b * L::kAccStride);
+        if (t >= 2 && !mbar_wait(barAccEmpty + b, (uint32_t)((t / 2 - 1) & 1))) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned char* b_hi = sB + c * L::kBChunk;
-        const unsigned char* b_lo = sB + (kMaxChunks + c) * L::kBChunk;
+        for (int c = 0; c < nchunks; ++c, ++j) {
+          const int s = j % S;
+          if (!mbar_wait(barSplit + s, (uint32_t)((j / S) & 1))) { *abort_flag = 1; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned char* a_hi = sA + s * 2 * L::kAChunk;
+          const unsigned char* a_lo = a_hi + L::kAChunk;
+          const unsigned char* b_hi = sB + c * L::kBChunk;
+          const unsigned char* b_lo = sB + (kMaxChunks + c) * L::kBChunk;
 #pragma unroll
-        for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per instruction: 32 bytes along the row
-          const uint64_t ah = smem_desc(a_hi + kk * 32), al = smem_desc(a_lo + kk * 32);
-          const uint64_t bh = smem_desc(b_hi + kk * 32), bl = smem_desc(b_lo + kk * 32);
-          mma_tf32(tmem, ah, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(tmem, ah, bl, idesc, 1u);
-          mma_tf32(tmem, al, bh, idesc, 1u);
+          for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per instruction: 32 bytes along the row
+            const uint64_t ah = smem_desc(a_hi + kk * 32), al = smem_desc(a_lo + kk * 32);
+            const uint64_t bh = smem_desc(b_hi + kk * 32), bl = smem_desc(b_lo + kk * 32);
+            mma_tf32(acc, ah, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(acc, ah, bl, idesc, 1u);
+            mma_tf32(acc, al, bh, idesc, 1u);
+          }
+          mma_commit(barEmpty + s);
+          if (c == nchunks - 1) mma_commit(barAccFull + b);
         }
-        mma_commit(barFree + s);
-        if (c == nchunks - 1) mma_commit(barAcc);
       }
     }
-    __syncthreads();
-    if (s_abort) break;
-    if (!mbar_wait(barAcc, acc_phase)) s_abort = 1;
-    acc_phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp < 4 && !s_abort) {  // warp w reads tensor-memory lanes 32w .. 32w + 31
-      const int64_t row = (int64_t)tile * kBM + warp * 32 + lane;
+  } else {  // warps 4-7: store the tiles
+    const int q = warp - 4;
+    for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
+      const int b = t & 1;
+      if (!mbar_wait(barAccFull + b, (uint32_t)((t / 2) & 1))) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int tile = blockIdx.x + t * gridDim.x;
+      const int64_t row = (int64_t)tile * kBM + q * 32 + lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < NPAD; c0 += 16) {
         uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * L::kAccStride + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -246,32 +273,31 @@ k_lift_tf32x3(int M, int N, int K, const __grid_constant__ CUtensorMap mapA,
           float* dst = C + row * ldc + c0;
           if (c0 + 16 <= N) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              reinterpret_cast<float4*>(dst)[q] =
-                  make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                              __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            for (int u = 0; u < 4; ++u)
+              reinterpret_cast<float4*>(dst)[u] =
+                  make_float4(__uint_as_float(v[4 * u]), __uint_as_float(v[4 * u + 1]),
+                              __uint_as_float(v[4 * u + 2]), __uint_as_float(v[4 * u + 3]));
           } else {
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (c0 + q < N) dst[q] = __uint_as_float(v[q]);
+            for (int u = 0; u < 16; ++u)
+              if (c0 + u < N) dst[u] = __uint_as_float(v[u]);
           }
         }
       }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (s_abort) {
-      atomicOr(status, FLAG_TC_TIMEOUT);
-      // nothing issued may still write shared or tensor memory: bounded waits for the
-      // last MMA commit of each stage
-      for (int s = 0; s < 2; ++s)
-        if (issued[s]) mbar_wait(barFree + s, free_phase[s]);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(barAccEmpty + b)) : "memory");
     }
   }
   __syncthreads();
-  if (warp == 0) {
+  if (tid == 0 && *abort_flag) atomicOr(status, FLAG_TC_TIMEOUT);
+  if (warp == 1) {
+    // no MMA may still write the accumulators when they are released (bounded wait for a
+    // commit that tracks everything issued)
+    if (lane == 0 && *abort_flag) {
+      mma_commit(barDrain);
+      mbar_wait(barDrain, 0);
+    }
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)L::tmem_cols)
