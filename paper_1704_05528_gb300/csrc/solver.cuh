@@ -212,6 +212,19 @@ __global__ void k_scale_cols(int r, int k, int kp, const double* __restrict__ Ub
   }
 }
 
+// dst (rows x ld, binary64) = src[:, :k] diag(scale) and zero columns k .. ld-1
+template <typename T>
+__global__ void k_export_scaled(int64_t rows, int k, int ld, const T* __restrict__ src, int64_t lds,
+                                const double* __restrict__ scale, double* __restrict__ dst) {
+  const int64_t total = rows * ld;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ld;
+    const int j = (int)(t - i * ld);
+    dst[t] = j < k ? (double)src[i * lds + j] * scale[j] : 0.0;
+  }
+}
+
 __global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ ss,
                             double* __restrict__ v) {
   const double inv = 1.0 / sqrt(ss[0]);
@@ -279,6 +292,8 @@ struct Work {
   // doubles for the graph's copies.  Off unless the caller provides host_pin.
   double* host_pin = nullptr;
   bool graph_broken = false;
+  // the eigen-phase graph of the next R4SVD call was launched ahead by the caller
+  bool graph_inflight = false;
   uint64_t graph_clock = 0;
   EigGraph eg[2];
   // graphs are recorded on a private stream (the caller's may be the legacy default
@@ -287,7 +302,9 @@ struct Work {
     cudaStream_t s = nullptr;
     ~OwnedStream() { if (s) cudaStreamDestroy(s); }
   } cap;
-  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + kFlagWords; }
+  // [0, 2 r_cap + kFlagWords) for the graph's copies, then 4 doubles for the caller
+  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + kFlagWords + 4; }
+  double* pin_tail() const { return host_pin + 2 * (size_t)P.r_cap + kFlagWords; }
 
   void layout(Arena& a) {
     const int64_t m = P.m, n = P.n, z = pat->nnz;
@@ -572,8 +589,9 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   // run the whole eigen phase as one graph and check that assumption afterwards.
   bool have_normB = false;
   if (s > 0 && W.bt_ready) {
-    bool ran = false;
-    SVT_TRY(eig_phase_graph<T>(W, Q, s, Unew, &ran));
+    bool ran = W.graph_inflight;  // launched ahead with these buffers by the caller
+    W.graph_inflight = false;
+    if (!ran) SVT_TRY(eig_phase_graph<T>(W, Q, s, Unew, &ran));
     if (ran) {
       have_normB = true;
       SVT_CUDA(cudaStreamSynchronize(st));
@@ -705,26 +723,37 @@ svt_status scaled_right(Work<T>& W, int r, int k, const std::vector<double>& coe
       r, k, kp, W.Ub, r, W.coef, W.Tsm);
   SVT_LAUNCH_CHECK();
   SVT_PROF("lift_V", gemm_bytes(W.P.n, r, k, (int)sizeof(T), false), W.s);
+  if constexpr (sizeof(T) == 4) {  // the same contraction shape as the lift of U
+    if (W.tcb && lift_tc_fits(W.P.n, r, kp, W.Bt, W.ldb, W.Wk, W.ldk))
+      return lift_tc(W.P.n, r, kp, W.Bt, W.ldb, W.Tsm, kp, W.Wk, W.ldk, W.tcb, W.flags + 4, W.s);
+  }
   SVT_TRY((gemm_nn<T, T>(W.P.n, r, kp, 1.0, W.Bt, W.ldb, W.Tsm, kp, 0.0, nullptr, 0, W.Wk, W.ldk, W.s)));
   return SVT_OK;
 }
 
 // Copy the first k columns of a device T matrix into caller memory (double, ld = cap).
+// With col_scale (device, k values) column j is multiplied by col_scale[j] in binary64.
 template <typename T>
 svt_status export_cols(Work<T>& W, int64_t rows, int k, const T* src, int64_t lds, double* dst,
-                       int cap) {
+                       int cap, const double* col_scale = nullptr) {
   if (rows <= 0 || cap <= 0) return SVT_OK;
+  auto fill = [&](double* d) -> svt_status {
+    if (col_scale && k > 0) {
+      const int64_t total = rows * cap;
+      k_export_scaled<T><<<(int)std::min<int64_t>(ceil_div(total, 256), 4096), 256, 0, W.s>>>(
+          rows, k, cap, src, lds, col_scale, d);
+      SVT_LAUNCH_CHECK();
+      return SVT_OK;
+    }
+    SVT_CUDA(cudaMemsetAsync(d, 0, rows * cap * sizeof(double), W.s));
+    return copy_convert<T, double>(rows, k, src, lds, d, cap, W.s);
+  };
   const bool dev = is_device_pointer(dst);
-  if (dev) {
-    SVT_CUDA(cudaMemsetAsync(dst, 0, rows * cap * sizeof(double), W.s));
-    SVT_TRY((copy_convert<T, double>(rows, k, src, lds, dst, cap, W.s)));
-    return SVT_OK;
-  }
+  if (dev) return fill(dst);
   DeviceBlock tmp;
   SVT_TRY(tmp.alloc(rows * cap * sizeof(double), W.s));
   double* d = (double*)tmp.ptr;
-  SVT_CUDA(cudaMemsetAsync(d, 0, rows * cap * sizeof(double), W.s));
-  SVT_TRY((copy_convert<T, double>(rows, k, src, lds, d, cap, W.s)));
+  SVT_TRY(fill(d));
   SVT_CUDA(cudaMemcpyAsync(dst, d, rows * cap * sizeof(double), cudaMemcpyDeviceToHost, W.s));
   SVT_CUDA(cudaStreamSynchronize(W.s));
   return SVT_OK;

@@ -180,8 +180,14 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   // page-locked host words for the copies inside the captured eigen phase
   struct HostPin {
     void* p = nullptr;
-    ~HostPin() { if (p) cudaFreeHost(p); }
+    cudaStream_t s = nullptr;
+    ~HostPin() {
+      if (!p) return;
+      cudaStreamSynchronize(s);  // a graph launched ahead may still copy into it
+      cudaFreeHost(p);
+    }
   } pin;
+  pin.s = st;
   SVT_CUDA(cudaMallocHost(&pin.p, Work<T>::pin_doubles(P.r_cap) * sizeof(double)));
   Work<T> W;
   W.P = P; W.pat = pat; W.s = st;
@@ -265,12 +271,14 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   svt_status status = SVT_NOT_CONVERGED;
   std::vector<double> coef;
   bool fused = false;
+  struct Event {
+    cudaEvent_t e = nullptr;
+    ~Event() { if (e) cudaEventDestroy(e); }
+  } upd;
+  SVT_CUDA(cudaEventCreateWithFlags(&upd.e, cudaEventDisableTiming));
+  double* hsum = W.pin_tail();  // sums of the update, then its status word
   for (int i = 1; i <= maxit; ++i) {
     const auto t_it = clk::now();
-    if (fused) {  // the last update formed Y^T U for this iteration's recycled basis
-      std::swap(W.Bt, bt_alt);
-      W.bt_ready = true;
-    }
     SVT_TRY(r4svd_run<T>(W, y_csr, W.y_csc, Qcur, s, normY2, eps_thr, (uint32_t)i, Qnext, &ro));
     const int r = ro.r;
     k = 0;
@@ -296,10 +304,29 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
       SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
                                 W.part, W.flags, st, true));
     }
+    SVT_CUDA(cudaMemcpyAsync(hsum, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaMemcpyAsync(hsum + 3, W.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaMemcpyAsync(reinterpret_cast<unsigned*>(hsum + 3) + 1, W.flags + 4, sizeof(unsigned),
+                             cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaEventRecord(upd.e, st));
+    if (fused) {  // the update formed Y^T U for the next iteration's recycled basis
+      std::swap(W.Bt, bt_alt);
+      W.bt_ready = true;
+      // the next R4SVD call most likely needs no new block: launch its eigen phase now,
+      // before this iteration's residual is known (r4svd_run checks the assumption)
+      if (i < maxit) {
+        bool ran = false;
+        SVT_TRY(eig_phase_graph<T>(W, Qnext, r, Qcur, &ran));
+        W.graph_inflight = ran;
+      }
+    }
+    SVT_CUDA(cudaEventSynchronize(upd.e));
     double sums[3];
-    unsigned fl = 0;
-    SVT_CUDA(cudaMemcpyAsync(sums, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SVT_TRY(read_flags(W, &fl));
+    unsigned fl = 0, fl_tc = 0;
+    memcpy(sums, hsum, sizeof(sums));
+    memcpy(&fl, hsum + 3, sizeof(unsigned));
+    memcpy(&fl_tc, reinterpret_cast<const unsigned*>(hsum + 3) + 1, sizeof(unsigned));
+    if (fl_tc & FLAG_TC_TIMEOUT) return fail(SVT_ERR_CUDA, "tensor-core lift: a bounded wait ran out");
     rel = std::sqrt(sums[0]) / nA;
     mae = sums[1] / (double)nnz;
     if (!std::isfinite(rel) || (fl & FLAG_NONFINITE))
@@ -339,14 +366,16 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     res->seconds_total = seconds_since(t_start);
     return status;
   }
-  // X = U_K diag(sigma_K - tau) V_K^T with V_K = B^T U_B,K Sigma_K^-1
+  // X = U_K diag(sigma_K - tau) V_K^T with V_K = B^T U_B,K Sigma_K^-1.  The last update used
+  // W = B^T U_B,K diag((sigma_K - tau) / sigma_K), so V_K = W diag(1 / (sigma_K - tau)); the
+  // buffers of the eigen phase may already hold the next (speculated) iteration.
   std::vector<double> inv(k), shrunk(cap, 0.0);
-  for (int j = 0; j < k; ++j) { inv[j] = 1.0 / ro.sigma[j]; shrunk[j] = ro.sigma[j] - tau; }
-  SVT_TRY(scaled_right<T>(W, ro.r, k, inv));
+  for (int j = 0; j < k; ++j) { inv[j] = 1.0 / (ro.sigma[j] - tau); shrunk[j] = ro.sigma[j] - tau; }
+  if (k > 0) SVT_CUDA(cudaMemcpyAsync(W.coef, inv.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
   T* Ufinal = (last_iter > 0 && status == SVT_OK) ? Qnext : Qcur;
   // after a converged break Qnext holds U; after the loop ran out, the swap moved it to Qcur
   SVT_TRY(export_cols<T>(W, m, k, Ufinal, W.ldq, Uo, cap));
-  SVT_TRY(export_cols<T>(W, n, k, W.Wk, W.ldk, Vo, cap));
+  SVT_TRY(export_cols<T>(W, n, k, W.Wk, W.ldk, Vo, cap, W.coef));
   if (So) SVT_CUDA(cudaMemcpyAsync(So, shrunk.data(), cap * sizeof(double), cudaMemcpyDefault, st));
   SVT_CUDA(cudaStreamSynchronize(st));
   prof_flush();
