@@ -49,6 +49,11 @@ def parse_args():
     ap.add_argument("--maxit", type=int, default=None)
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # variants of Section 2 for sweeps (the headline uses the paper's settings)
+    ap.add_argument("--recycle", default="all", choices=["all", "kept", "none"])
+    ap.add_argument("--n-power", type=int, default=None)
+    ap.add_argument("--fixed-rank", type=int, default=0,
+                    help="t = r_max = this and no recycling: the fixed-rank randomized SVD")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -252,7 +257,11 @@ def our_arm(args):
     cols = torch.from_numpy(w.cols).cuda()
     vals = torch.from_numpy(w.vals).to(device="cuda", dtype=vdt)
     kw = dict(t=w.t, dt=w.dt, n_power=w.n_power, beta=w.beta, eps_thr0=w.eps_thr0, r_max=w.r_max,
-              seed=w.seed)
+              seed=w.seed, recycle=args.recycle)
+    if args.n_power is not None:
+        kw["n_power"] = args.n_power
+    if args.fixed_rank > 0:
+        kw.update(t=args.fixed_rank, r_max=args.fixed_rank, recycle="none")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -315,13 +324,17 @@ def our_arm(args):
     vals_h = torch.from_numpy(w.vals).to(vdt).pin_memory()
     r_cap = min(w.m, w.n, w.r_max) if w.r_max > 0 else min(w.m, w.n)
     e2e_steps = max(1, min(args.steps, 2))
+
+    def e2e_solve():
+        return svt.complete(w.m, w.n, rows_h, cols_h, vals_h, w.tau, w.delta, w.tol, maxit,
+                            precision=prec, log=False, on_host=True, **kw)
+    e2e_solve()  # untimed: first use of the host-buffer path (page faults on fresh outputs)
     barrier()
     t0 = time.perf_counter()
     e2e_iters = 0
     for _ in range(e2e_steps):
         flush_l2(flush)
-        r = svt.complete(w.m, w.n, rows_h, cols_h, vals_h, w.tau, w.delta, w.tol, maxit, precision=prec,
-                         log=False, on_host=True, **kw)
+        r = e2e_solve()
         e2e_iters += r.iters
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -375,8 +388,9 @@ def our_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "m": w.m, "n": w.n, "nnz_train": w.nnz, "r_max": w.r_max,
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "nnz_train": w.nnz, "r_max": kw["r_max"],
                        "tau": w.tau, "delta": w.delta, "tol": w.tol, "maxit": maxit,
+                       "recycle": kw["recycle"], "n_power": kw["n_power"], "t": kw["t"],
                        "precision": "mixed fp32 (binary64 Gram/eigen/norms)" if prec == "mixed" else "fp64",
                        "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) before each step",
                        "iters_per_step": total_iters / world / args.steps},

@@ -55,6 +55,17 @@ typedef enum svt_precision {
   SVT_MIXED_FP32 = 1
 } svt_precision;
 
+/* Which left singular vectors of D_tau's SVD seed the next R4SVD call (Section 2.3).
+ * SVT_RECYCLE_ALL is the paper's method (Algorithm 3 with the r revealed vectors).
+ * SVT_RECYCLE_KEPT recycles only the k vectors above tau.  SVT_RECYCLE_NONE starts every
+ * call from Gaussian blocks (Algorithm 2); with t = r_max that is the fixed-rank
+ * randomized SVD of Section 2.1 (one block of r_max columns, n_power power iterations). */
+typedef enum svt_recycle {
+  SVT_RECYCLE_ALL = 0,
+  SVT_RECYCLE_KEPT = 1,
+  SVT_RECYCLE_NONE = 2
+} svt_recycle;
+
 /* Solver options.  Defaults (svt_default_options) follow Section 3: t =
  * floor(0.05 min(m,n)), dt = 10, beta = 0.95; no power iterations. */
 typedef struct svt_options {
@@ -64,6 +75,8 @@ typedef struct svt_options {
   int32_t r_max;        /* rank cap; r <= min(m, n, r_max); <= 0: min(m, n)            */
   int32_t power_steps;  /* power steps for ||P_Lambda(A)||_2 in the initialisation     */
   int32_t precision;    /* svt_precision                                               */
+  int32_t recycle;      /* svt_recycle (svt_complete)                                   */
+  int32_t reserved;     /* must be 0                                                   */
   double beta;          /* cooling factor for the precision threshold (0 < beta < 1)   */
   double eps_thr0;      /* initial error-percentage threshold                          */
   uint64_t seed;        /* key of the counter-based Gaussian generator                 */

@@ -257,10 +257,17 @@ class SVTResult:
 
 def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=0,
         beta=0.95, eps_thr0=0.9, r_max=0, seed=0x5EED, power_steps=100,
-        keep_history=False) -> SVTResult:
-    """Algorithm 4 (fast SVT with R4SVD) on the observed entries (rows, cols, vals)."""
+        keep_history=False, recycle="all") -> SVTResult:
+    """Algorithm 4 (fast SVT with R4SVD) on the observed entries (rows, cols, vals).
+
+    recycle picks the basis handed to the next R4SVD call (Section 2.3): "all" the r
+    revealed left singular vectors (Algorithm 3, the paper's method), "kept" the k above
+    tau, "none" no basis (Algorithm 2 every iteration; with t = r_max a fixed-rank
+    randomized SVD as in Section 2.1)."""
     if not (tau > 0 and delta > 0) or maxit < 0 or dt <= 0 or not (0 < beta < 1):
         raise OracleError("arg", "bad scalar parameter")
+    if recycle not in ("all", "kept", "none"):
+        raise OracleError("arg", "recycle must be all, kept or none")
     p = build_pattern(m, n, rows, cols)
     vals = np.asarray(vals, dtype=np.float64).ravel()
     if vals.shape[0] != p.nnz:
@@ -317,7 +324,7 @@ def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=
         if rel < tol:
             return res
         y = y + delta * d                                    # Y <- Y + delta P_Lambda(A - X)
-        U_prev = rs.U
+        U_prev = {"all": rs.U, "kept": rs.U[:, keep], "none": None}[recycle]
     if res is None:                                          # maxit == 0
         empty.status = "not_converged"
         return empty

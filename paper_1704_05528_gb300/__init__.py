@@ -66,7 +66,13 @@ def _stream_ptr():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+RECYCLE = {"all": 0, "kept": 1, "none": 2}
+
+
 def options(precision="fp64", **kw) -> L.Options:
+    """svt_options with the library defaults, then the given fields.  recycle may be
+    "all" (Algorithm 3), "kept" or "none" (Algorithm 2 every call; with t = r_max the
+    fixed-rank randomized SVD)."""
     lib = library()
     o = L.Options()
     lib.svt_default_options(C.byref(o))
@@ -74,6 +80,10 @@ def options(precision="fp64", **kw) -> L.Options:
     for key, val in kw.items():
         if key == "t" and val is None:
             continue
+        if key == "recycle" and isinstance(val, str):
+            if val not in RECYCLE:
+                raise ValueError(f"recycle must be one of {sorted(RECYCLE)}")
+            val = RECYCLE[val]
         if not hasattr(o, key):
             raise TypeError(f"unknown option {key}")
         setattr(o, key, val)

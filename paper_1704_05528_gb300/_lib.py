@@ -19,7 +19,7 @@ SVT_FP64, SVT_MIXED_FP32 = 0, 1
 class Options(C.Structure):
     _fields_ = [("t", C.c_int32), ("dt", C.c_int32), ("n_power", C.c_int32),
                 ("r_max", C.c_int32), ("power_steps", C.c_int32), ("precision", C.c_int32),
-                ("beta", C.c_double), ("eps_thr0", C.c_double), ("seed", C.c_uint64),
+                ("recycle", C.c_int32), ("reserved", C.c_int32), ("beta", C.c_double), ("eps_thr0", C.c_double), ("seed", C.c_uint64),
                 ("stream", C.c_void_p)]
 
 

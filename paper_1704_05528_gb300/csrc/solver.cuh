@@ -173,7 +173,7 @@ constexpr double near_diagonal_tol() { return sizeof(T) == 8 ? 1e-12 : 1e-8; }
 
 struct Params {
   int64_t m, n;
-  int r_cap, t_eff, dt, np, power_steps;
+  int r_cap, t_eff, dt, np, power_steps, recycle;
   double beta, eps_thr0;
   uint64_t seed;
 };
@@ -184,6 +184,8 @@ inline svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params
     return fail(SVT_ERR_ARG, "options: need dt > 0, n_power >= 0, 0 < beta < 1, power_steps >= 1");
   if (o->precision != SVT_FP64 && o->precision != SVT_MIXED_FP32)
     return fail(SVT_ERR_ARG, "options: unknown precision %d", o->precision);
+  if (o->recycle < SVT_RECYCLE_ALL || o->recycle > SVT_RECYCLE_NONE || o->reserved != 0)
+    return fail(SVT_ERR_ARG, "options: unknown recycle mode %d (or reserved field set)", o->recycle);
   const int64_t mn = std::min(m, n);
   int64_t cap = o->r_max > 0 ? std::min<int64_t>(mn, o->r_max) : mn;
   if (cap > 1024)
@@ -192,7 +194,7 @@ inline svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params
   int64_t t = o->t > 0 ? o->t : (int64_t)std::floor(0.05 * (double)mn);
   if (t < 1) t = 1;
   P->m = m; P->n = n; P->r_cap = (int)cap; P->t_eff = (int)std::min<int64_t>(t, 1 << 20);
-  P->dt = o->dt; P->np = o->n_power; P->power_steps = o->power_steps;
+  P->dt = o->dt; P->np = o->n_power; P->power_steps = o->power_steps; P->recycle = o->recycle;
   P->beta = o->beta; P->eps_thr0 = o->eps_thr0; P->seed = o->seed;
   return SVT_OK;
 }

@@ -287,13 +287,15 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     for (int j = 0; j < k; ++j) coef[j] = (ro.sigma[j] - tau) / ro.sigma[j];
     SVT_TRY(scaled_right<T>(W, r, k, coef));
     SVT_CUDA(cudaMemsetAsync(W.flags, 0, sizeof(unsigned), st));
-    // U (= Qnext, r columns) is the next iteration's recycled basis: in CSC order the
-    // update also forms B^T = Y^T U for it
-    fused = update_recycle_fits<T>(r, nnz);
+    // The first s_next columns of U (= Qnext) seed the next R4SVD call: all r of them
+    // (Algorithm 3), the k kept ones, or none.  In CSC order the update also forms
+    // B^T = Y^T U[:, :s_next] for that call.
+    const int s_next = P.recycle == SVT_RECYCLE_ALL ? r : P.recycle == SVT_RECYCLE_KEPT ? k : 0;
+    fused = s_next > 0 && update_recycle_fits<T>(s_next, nnz);
     if (fused) {
-      SVT_PROF("update_recycled", recycle_bytes(nnz, m, n, k, r, (int)sizeof(T)), st);
-      SVT_TRY(update_recycle<T>(pat, Qnext, W.ldq, r, W.Wk, W.ldk, k, a_csc, W.y_csc, delta, bt_alt,
-                                ldb_alt, W.dsc + 5, fpart, W.flags, W.spmm_scr, st));
+      SVT_PROF("update_recycled", recycle_bytes(nnz, m, n, k, s_next, (int)sizeof(T)), st);
+      SVT_TRY(update_recycle<T>(pat, Qnext, W.ldq, s_next, W.Wk, W.ldk, k, a_csc, W.y_csc, delta,
+                                bt_alt, ldb_alt, W.dsc + 5, fpart, W.flags, W.spmm_scr, st));
       W.y_csr_stale = y_csr;
     } else {
       if (W.y_csr_stale) {
@@ -316,7 +318,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
       // before this iteration's residual is known (r4svd_run checks the assumption)
       if (i < maxit) {
         bool ran = false;
-        SVT_TRY(eig_phase_graph<T>(W, Qnext, r, Qcur, &ran));
+        SVT_TRY(eig_phase_graph<T>(W, Qnext, s_next, Qcur, &ran));
         W.graph_inflight = ran;
       }
     }
@@ -353,7 +355,7 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     prof_flush();
     normY2 = sums[2];
     std::swap(Qcur, Qnext);
-    s = r;
+    s = s_next;
   }
   res->iters = last_iter;
   res->k = k;
@@ -431,7 +433,7 @@ svt_status r4svd_impl(const svt_pattern* p, const T* y_csr, const T* U_prev, int
 }  // namespace svt
 
 // ====================================================================== C ABI
-extern "C" int svt_abi_version(void) { return 1; }
+extern "C" int svt_abi_version(void) { return 2; }
 
 extern "C" void svt_default_options(svt_options* o) {
   if (!o) return;
@@ -441,6 +443,8 @@ extern "C" void svt_default_options(svt_options* o) {
   o->r_max = 0;
   o->power_steps = 100;
   o->precision = SVT_FP64;
+  o->recycle = SVT_RECYCLE_ALL;
+  o->reserved = 0;
   o->beta = 0.95;
   o->eps_thr0 = 0.9;
   o->seed = 0x5EEDull;

@@ -429,6 +429,31 @@ def test_complete_fp64_above_fused_rank(svt, torch_mod):
     _assert_fp64_parity(w, ref, got)
 
 
+@pytest.mark.parametrize("recycle,over", [
+    ("kept", {}),
+    ("none", {}),
+    ("none", {"t": 30, "r_max": 30, "n_power": 1}),   # fixed-rank randomized SVD
+])
+def test_complete_fp64_recycle_variants(svt, torch_mod, recycle, over):
+    """Recycling only the kept singular vectors, or none (Algorithm 2 every iteration; with
+    t = r_max the fixed-rank randomized SVD): identical per-iteration ranks, blocks and
+    cooling, and the same completion as the oracle."""
+    w = workloads.random_lowrank(300, 250, 8, 0.3, seed=23, n_hold=200, maxit=25)
+    ref, got = _run_pair(svt, torch_mod, w, w.maxit, "fp64", recycle=recycle, **over)
+    if recycle == "none":
+        assert all(e["blocks"] >= 1 for e in ref.log)
+    _assert_fp64_parity(w, ref, got)
+
+
+def test_complete_mixed_recycle_kept(svt, torch_mod):
+    w = workloads.make("lowrank500")
+    ref, got = _run_pair(svt, torch_mod, w, 40, "mixed", recycle="kept")
+    p = ref.pattern
+    x_obs_ref = _completed(ref.U, ref.S, ref.V, p.csr_rows(), p.col_idx)
+    x_obs_got = _completed(got.U, got.S, got.V, p.csr_rows(), p.col_idx)
+    assert _rel(x_obs_got, x_obs_ref) < MIXED_TOL
+
+
 def test_complete_fp64_lowrank500(svt, torch_mod):
     """500x500 rank-10, 20% observed: the full 200-iteration run."""
     w = workloads.small_lowrank()

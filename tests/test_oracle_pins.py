@@ -238,6 +238,49 @@ def test_r4svd_power_iteration_improves_subspace():
     assert np.sum(s_true[:6] - r2.S) < np.sum(s_true[:6] - r0.S)
 
 
+@pytest.mark.parametrize("n_power", [0, 2])
+def test_r4svd_fixed_rank_is_the_textbook_randomized_svd(n_power):
+    """Without a recycled basis and with t = r_cap, R4SVD takes one Gaussian block and is
+    the fixed-rank randomized SVD of Section 2.1: X = Y Omega (with power iterations
+    X <- Y Y^T X), Q an orthonormal basis of X, B = Q^T Y, SVD of B.  Written out here with
+    LAPACK's QR and SVD on the same Omega."""
+    rng = np.random.default_rng(41)
+    Y = _sparse_lowrank(rng, 90, 70, 12, 0.4)
+    T, seed, it = 15, 77, 3
+    ro = oracle.r4svd(Y, None, 0.5, it, t=T, dt=4, n_power=n_power, r_cap=T, seed=seed)
+    assert (ro.r, ro.blocks) == (T, 1)
+    X = Y.toarray() @ gaussian_block(seed, it, 0, Y.shape[1], T)
+    for _ in range(n_power):
+        X = Y.toarray() @ (Y.toarray().T @ X)
+    Q, _ = np.linalg.qr(X)
+    Ub, S, Vt = np.linalg.svd(Q.T @ Y.toarray(), full_matrices=False)
+    assert np.allclose(ro.S, S, rtol=1e-11, atol=1e-11 * S[0])
+    k = 10  # separated part: compare the rank-k reconstructions
+    assert np.allclose((ro.U[:, :k] * ro.S[:k]) @ ro.V[:, :k].T, ((Q @ Ub)[:, :k] * S[:k]) @ Vt[:k],
+                       atol=1e-10 * S[0])
+
+
+def test_svt_recycling_variants():
+    """Recycling only the kept vectors is recycling all of them when every revealed value is
+    kept; without recycling every R4SVD call draws blocks again (Algorithm 2 each time)."""
+    rng = np.random.default_rng(8)
+    m, n = 70, 60
+    M = rng.standard_normal((m, 3)) @ rng.standard_normal((3, n))
+    mask = rng.random((m, n)) < 0.5
+    rows, cols = np.nonzero(mask)
+    kw = dict(t=8, dt=4, eps_thr0=0.05, seed=5, r_max=30)
+    runs = {rc: oracle.svt(m, n, rows, cols, M[rows, cols], 1e-9, 1.2, 0.0, 6, recycle=rc, **kw)
+            for rc in ("all", "kept", "none")}
+    log_all, log_kept = runs["all"].log, runs["kept"].log
+    assert all(e["k"] == e["r"] for e in log_all)            # tau below every value
+    assert [(e["r"], e["blocks"]) for e in log_kept] == [(e["r"], e["blocks"]) for e in log_all]
+    assert np.allclose(runs["kept"].S, runs["all"].S, rtol=1e-12)
+    assert all(e["blocks"] >= 1 for e in runs["none"].log)
+    assert sum(e["blocks"] for e in runs["none"].log) > sum(e["blocks"] for e in log_all)
+    with pytest.raises(oracle.OracleError):
+        oracle.svt(m, n, rows, cols, M[rows, cols], 1.0, 1.2, 0.0, 2, recycle="some")
+
+
 def test_r4svd_rank_cap_and_exhaustion():
     rng = np.random.default_rng(23)
     # rank-3 matrix with a full pattern: the range is exhausted after 3 directions
