@@ -54,8 +54,25 @@ def parse_args():
     ap.add_argument("--n-power", type=int, default=None)
     ap.add_argument("--fixed-rank", type=int, default=0,
                     help="t = r_max = this and no recycling: the fixed-rank randomized SVD")
+    ap.add_argument("--stop", default="residual", choices=["residual", "mae"])
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--eval", action="store_true",
+                    help="log the held-out MAE of every iteration (an analysis run, not the headline)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
+
+
+def eval_summary(res):
+    """Training and held-out MAE along the last timed solve (the curves of Section 3.2)."""
+    me = [e["mae_eval"] for e in res.log]
+    best = min(range(len(me)), key=lambda i: me[i]) if me else None
+    pick = sorted(set([0, len(me) // 4, len(me) // 2, 3 * len(me) // 4, len(me) - 1, best or 0]))
+    return {"iters": res.iters, "best_iter": None if best is None else best + 1,
+            "best_mae_eval": None if best is None else me[best],
+            "final_mae_train": res.log[-1]["mae"] if res.log else None,
+            "final_mae_eval": me[-1] if me else None,
+            "curve": [{"iter": i + 1, "mae_train": res.log[i]["mae"], "mae_eval": me[i],
+                       "seconds": res.log[i]["seconds"]} for i in pick] if me else []}
 
 
 def dist_env():
@@ -265,9 +282,15 @@ def our_arm(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tol = w.tol if args.tol is None else args.tol
+    kw["stop"] = args.stop
+    ev_set = None
+    if args.eval:
+        ev_set = (w.held_rows, w.held_cols, w.held_vals if prec == "fp64" else w.held_vals.astype(np.float32))
+
     def solve(p=prec, v=vals, mi=maxit):
-        return svt.complete(w.m, w.n, rows, cols, v, w.tau, w.delta, w.tol, mi, precision=p, log=False,
-                            **kw)
+        return svt.complete(w.m, w.n, rows, cols, v, w.tau, w.delta, tol, mi, precision=p,
+                            log=ev_set is not None, eval_set=ev_set, **kw)
 
     for _ in range(args.warmup):
         solve()
@@ -288,6 +311,7 @@ def our_arm(args):
         iters += res.iters
         if res.converged:
             conv_times.append(time.perf_counter() - t0)
+        last_res = res
     ev1.record(stream)
     barrier()
     clock_info = clocks.stop()
@@ -326,7 +350,7 @@ def our_arm(args):
     e2e_steps = max(1, min(args.steps, 2))
 
     def e2e_solve():
-        return svt.complete(w.m, w.n, rows_h, cols_h, vals_h, w.tau, w.delta, w.tol, maxit,
+        return svt.complete(w.m, w.n, rows_h, cols_h, vals_h, w.tau, w.delta, tol, maxit,
                             precision=prec, log=False, on_host=True, **kw)
     e2e_solve()  # untimed: first use of the host-buffer path (page faults on fresh outputs)
     barrier()
@@ -389,12 +413,13 @@ def our_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "nnz_train": w.nnz, "r_max": kw["r_max"],
-                       "tau": w.tau, "delta": w.delta, "tol": w.tol, "maxit": maxit,
+                       "tau": w.tau, "delta": w.delta, "tol": tol, "stop": args.stop, "maxit": maxit,
                        "recycle": kw["recycle"], "n_power": kw["n_power"], "t": kw["t"],
                        "precision": "mixed fp32 (binary64 Gram/eigen/norms)" if prec == "mixed" else "fp64",
                        "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) before each step",
                        "iters_per_step": total_iters / world / args.steps},
             "time_to_tol_s": statistics.mean(conv_times) if conv_times else None,
+            "eval": eval_summary(last_res) if ev_set is not None else None,
             "fp64_leg": fp64_leg,
             "gpu_launches": kernel_launches,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -66,6 +66,15 @@ typedef enum svt_recycle {
   SVT_RECYCLE_NONE = 2
 } svt_recycle;
 
+/* Stop rule of svt_complete: SVT_STOP_RESIDUAL ends when the relative residual
+ * ||P_Lambda(A - X^(i))||_F / ||P_Lambda(A)||_F falls below tol (Algorithm 4);
+ * SVT_STOP_MAE when the mean absolute error over the observed entries,
+ * (1/|Lambda|) sum |A_ij - X^(i)_ij|, falls below tol (the rule of Section 3). */
+typedef enum svt_stop {
+  SVT_STOP_RESIDUAL = 0,
+  SVT_STOP_MAE = 1
+} svt_stop;
+
 /* Solver options.  Defaults (svt_default_options) follow Section 3: t =
  * floor(0.05 min(m,n)), dt = 10, beta = 0.95; no power iterations. */
 typedef struct svt_options {
@@ -76,7 +85,7 @@ typedef struct svt_options {
   int32_t power_steps;  /* power steps for ||P_Lambda(A)||_2 in the initialisation     */
   int32_t precision;    /* svt_precision                                               */
   int32_t recycle;      /* svt_recycle (svt_complete)                                   */
-  int32_t reserved;     /* must be 0                                                   */
+  int32_t stop;         /* svt_stop (svt_complete)                                      */
   double beta;          /* cooling factor for the precision threshold (0 < beta < 1)   */
   double eps_thr0;      /* initial error-percentage threshold                          */
   uint64_t seed;        /* key of the counter-based Gaussian generator                 */
@@ -97,6 +106,8 @@ typedef struct svt_iter_log {
   double mae;           /* mean |A - X^(i)| over the observed entries                  */
   double sigma_max;     /* largest singular value of Y^(i)                             */
   double seconds;       /* wall time of the iteration (host clock, after its sync)     */
+  double mae_eval;      /* mean |A - X^(i)| over the evaluation set of svt_complete_eval
+                           (entries outside Lambda), NaN without one                    */
 } svt_iter_log;
 
 typedef struct svt_result {
@@ -222,9 +233,9 @@ svt_status svt_r4svd(const svt_pattern* p, const void* y_csr, const void* U_prev
 /* Algorithm 4: complete the m x n matrix from nnz observed entries (rows, cols, vals).
  * rows/cols/vals may be host or device pointers (detected per pointer); vals is
  * double for SVT_FP64 and float for SVT_MIXED_FP32.  tau > 0 is the threshold of
- * eq. (3), delta > 0 the step of eq. (4); the iteration stops when the relative
- * residual ||P_Lambda(A - X^(i))||_F / ||P_Lambda(A)||_F falls below tol, or after
- * maxit iterations (SVT_NOT_CONVERGED).
+ * eq. (3), delta > 0 the step of eq. (4); the iteration stops when the quantity of
+ * opt->stop (by default the relative residual ||P_Lambda(A - X^(i))||_F /
+ * ||P_Lambda(A)||_F) falls below tol, or after maxit iterations (SVT_NOT_CONVERGED).
  * Output X = U diag(S) V^T with U (m x cap), S[cap], V (n x cap), binary64, row-major,
  * host or device memory; the first res->k columns are valid.  cap must be at least
  * min(m, n, r_max).  log (host, may be NULL) receives up to log_cap iteration records.
@@ -234,6 +245,20 @@ svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                         double tol, int32_t maxit, const svt_options* opt, double* U,
                         double* S, double* V, int32_t cap, svt_result* res,
                         svt_iter_log* log, int32_t log_cap);
+
+/* svt_complete with an evaluation set: n_eval entries (eval_rows, eval_cols, eval_vals;
+ * host or device, element type of vals) that the solver never reads as data.  After each
+ * iteration the mean absolute error of X^(i) on them goes to log[i].mae_eval: the
+ * held-out ("testing set") MAE curve of Section 3.2.  The entries need not be disjoint
+ * from Lambda, but must be distinct and in range (else SVT_ERR_DUPLICATE or
+ * SVT_ERR_INDEX).  n_eval = 0 gives svt_complete. */
+svt_status svt_complete_eval(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                             const int32_t* cols, const void* vals, int64_t n_eval,
+                             const int32_t* eval_rows, const int32_t* eval_cols,
+                             const void* eval_vals, double tau, double delta, double tol,
+                             int32_t maxit, const svt_options* opt, double* U, double* S,
+                             double* V, int32_t cap, svt_result* res, svt_iter_log* log,
+                             int32_t log_cap);
 
 /* ------------------------------------------------------------------ unrolled SVT */
 typedef struct svt_unrolled_params {

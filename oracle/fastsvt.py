@@ -257,17 +257,24 @@ class SVTResult:
 
 def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=0,
         beta=0.95, eps_thr0=0.9, r_max=0, seed=0x5EED, power_steps=100,
-        keep_history=False, recycle="all") -> SVTResult:
+        keep_history=False, recycle="all", stop="residual", eval_set=None) -> SVTResult:
     """Algorithm 4 (fast SVT with R4SVD) on the observed entries (rows, cols, vals).
 
     recycle picks the basis handed to the next R4SVD call (Section 2.3): "all" the r
     revealed left singular vectors (Algorithm 3, the paper's method), "kept" the k above
     tau, "none" no basis (Algorithm 2 every iteration; with t = r_max a fixed-rank
-    randomized SVD as in Section 2.1)."""
+    randomized SVD as in Section 2.1).
+
+    stop="residual" ends when ||P_Lambda(A - X)||_F / ||P_Lambda(A)||_F < tol (Algorithm 4),
+    stop="mae" when the mean |A - X| over Lambda < tol (the rule of Section 3).
+    eval_set = (rows, cols, vals) of held-out entries: each log entry gets "mae_eval", the
+    mean |A - X^(i)| over them (the testing-set curve of Section 3.2)."""
     if not (tau > 0 and delta > 0) or maxit < 0 or dt <= 0 or not (0 < beta < 1):
         raise OracleError("arg", "bad scalar parameter")
     if recycle not in ("all", "kept", "none"):
         raise OracleError("arg", "recycle must be all, kept or none")
+    if stop not in ("residual", "mae"):
+        raise OracleError("arg", "stop must be residual or mae")
     p = build_pattern(m, n, rows, cols)
     vals = np.asarray(vals, dtype=np.float64).ravel()
     if vals.shape[0] != p.nnz:
@@ -304,7 +311,12 @@ def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=
         d = a - x
         rel = float(np.sqrt(np.sum(d * d))) / nA
         mae = float(np.mean(np.abs(d)))
-        entry = dict(i=i, r=rs.r, k=int(keep.sum()), blocks=rs.blocks, eps=rs.eps,
+        mae_eval = math.nan
+        if eval_set is not None:                             # held-out MAE of X^(i)
+            er, ec, ev = eval_set
+            xe = sampled_product(Uk, Sk, Vk, np.asarray(er), np.asarray(ec))
+            mae_eval = float(np.mean(np.abs(np.asarray(ev, dtype=np.float64) - xe)))
+        entry = dict(i=i, r=rs.r, k=int(keep.sum()), blocks=rs.blocks, eps=rs.eps, mae_eval=mae_eval,
                      eps_thr=eps_thr, rel_residual=rel, mae=mae, exhausted=rs.exhausted,
                      sigma_max=float(rs.S[0]) if rs.r else 0.0,
                      margin_tau=float(np.min(np.abs(rs.S - tau))) if rs.r else math.inf,
@@ -321,7 +333,7 @@ def svt(m, n, rows, cols, vals, tau, delta, tol, maxit, *, t=-1, dt=10, n_power=
             entry["S"] = rs.S.copy()
         log.append(entry)
         res = SVTResult(Uk, Sk, Vk, int(keep.sum()), i, rel, "ok", k0, s2, log, y.copy(), p)
-        if rel < tol:
+        if (mae if stop == "mae" else rel) < tol:
             return res
         y = y + delta * d                                    # Y <- Y + delta P_Lambda(A - X)
         U_prev = {"all": rs.U, "kept": rs.U[:, keep], "none": None}[recycle]

@@ -67,6 +67,7 @@ def _stream_ptr():
 
 
 RECYCLE = {"all": 0, "kept": 1, "none": 2}
+STOP = {"residual": 0, "mae": 1}
 
 
 def options(precision="fp64", **kw) -> L.Options:
@@ -84,6 +85,10 @@ def options(precision="fp64", **kw) -> L.Options:
             if val not in RECYCLE:
                 raise ValueError(f"recycle must be one of {sorted(RECYCLE)}")
             val = RECYCLE[val]
+        if key == "stop" and isinstance(val, str):
+            if val not in STOP:
+                raise ValueError(f"stop must be one of {sorted(STOP)}")
+            val = STOP[val]
         if not hasattr(o, key):
             raise TypeError(f"unknown option {key}")
         setattr(o, key, val)
@@ -300,11 +305,14 @@ def _log_list(buf, n):
 
 
 def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", log=True,
-             on_host=None, **kw) -> Completion:
+             on_host=None, eval_set=None, **kw) -> Completion:
     """Algorithm 4 on (rows, cols, vals).
 
     Host inputs (numpy) are copied to the device inside the call and the factors come
     back as numpy arrays; device inputs (torch CUDA tensors) give device outputs.
+    eval_set = (rows, cols, vals) of held-out entries adds their MAE after every
+    iteration to the log ("mae_eval"); stop="mae" ends on the training MAE instead of the
+    relative residual.
     """
     torch = _torch()
     o = options(precision, **kw)
@@ -348,9 +356,19 @@ def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", l
     res = L.Result()
     log_cap = maxit if log else 0
     logbuf = (L.IterLog * max(log_cap, 1))()
-    st = library().svt_complete(m, n, nnz, *args, float(tau), float(delta), float(tol), int(maxit),
-                                C.byref(o), *outs, r_cap, C.byref(res), logbuf, log_cap)
-    del keep
+    eval_args, n_eval, keep_eval = [C.c_void_p(0)] * 3, 0, None
+    if eval_set is not None:
+        er, ec, ev = eval_set
+        np_dt = np.float64 if o.precision == FP64 else np.float32
+        keep_eval = (np.ascontiguousarray(np.asarray(er), dtype=np.int32),
+                     np.ascontiguousarray(np.asarray(ec), dtype=np.int32),
+                     np.ascontiguousarray(np.asarray(ev), dtype=np_dt))
+        eval_args = [a.ctypes.data_as(C.c_void_p) for a in keep_eval]
+        n_eval = keep_eval[0].shape[0]
+    st = library().svt_complete_eval(m, n, nnz, *args, n_eval, *eval_args, float(tau), float(delta),
+                                     float(tol), int(maxit), C.byref(o), *outs, r_cap, C.byref(res),
+                                     logbuf, log_cap)
+    del keep, keep_eval
     _check(st)
     k = res.k
     return Completion(U=U[:, :k], S=S[:k], V=V[:, :k], k=k, iters=res.iters, status=res.status,

@@ -19,7 +19,7 @@ SVT_FP64, SVT_MIXED_FP32 = 0, 1
 class Options(C.Structure):
     _fields_ = [("t", C.c_int32), ("dt", C.c_int32), ("n_power", C.c_int32),
                 ("r_max", C.c_int32), ("power_steps", C.c_int32), ("precision", C.c_int32),
-                ("recycle", C.c_int32), ("reserved", C.c_int32), ("beta", C.c_double), ("eps_thr0", C.c_double), ("seed", C.c_uint64),
+                ("recycle", C.c_int32), ("stop", C.c_int32), ("beta", C.c_double), ("eps_thr0", C.c_double), ("seed", C.c_uint64),
                 ("stream", C.c_void_p)]
 
 
@@ -27,7 +27,7 @@ class IterLog(C.Structure):
     _fields_ = [("iter", C.c_int32), ("r", C.c_int32), ("k", C.c_int32), ("blocks", C.c_int32),
                 ("cooled", C.c_int32), ("exhausted", C.c_int32), ("eps", C.c_double),
                 ("eps_thr", C.c_double), ("rel_residual", C.c_double), ("mae", C.c_double),
-                ("sigma_max", C.c_double), ("seconds", C.c_double)]
+                ("sigma_max", C.c_double), ("seconds", C.c_double), ("mae_eval", C.c_double)]
 
 
 class Result(C.Structure):
@@ -82,6 +82,9 @@ SIGNATURES = {
     "svt_complete": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _D, _D, _D, _I32,
                                C.POINTER(Options), _P, _P, _P, _I32, C.POINTER(Result),
                                C.POINTER(IterLog), _I32]),
+    "svt_complete_eval": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P, _D, _D, _D, _I32,
+                                    C.POINTER(Options), _P, _P, _P, _I32, C.POINTER(Result),
+                                    C.POINTER(IterLog), _I32]),
 }
 
 

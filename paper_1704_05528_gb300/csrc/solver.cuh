@@ -173,7 +173,7 @@ constexpr double near_diagonal_tol() { return sizeof(T) == 8 ? 1e-12 : 1e-8; }
 
 struct Params {
   int64_t m, n;
-  int r_cap, t_eff, dt, np, power_steps, recycle;
+  int r_cap, t_eff, dt, np, power_steps, recycle, stop;
   double beta, eps_thr0;
   uint64_t seed;
 };
@@ -184,8 +184,10 @@ inline svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params
     return fail(SVT_ERR_ARG, "options: need dt > 0, n_power >= 0, 0 < beta < 1, power_steps >= 1");
   if (o->precision != SVT_FP64 && o->precision != SVT_MIXED_FP32)
     return fail(SVT_ERR_ARG, "options: unknown precision %d", o->precision);
-  if (o->recycle < SVT_RECYCLE_ALL || o->recycle > SVT_RECYCLE_NONE || o->reserved != 0)
-    return fail(SVT_ERR_ARG, "options: unknown recycle mode %d (or reserved field set)", o->recycle);
+  if (o->recycle < SVT_RECYCLE_ALL || o->recycle > SVT_RECYCLE_NONE)
+    return fail(SVT_ERR_ARG, "options: unknown recycle mode %d", o->recycle);
+  if (o->stop != SVT_STOP_RESIDUAL && o->stop != SVT_STOP_MAE)
+    return fail(SVT_ERR_ARG, "options: unknown stop rule %d", o->stop);
   const int64_t mn = std::min(m, n);
   int64_t cap = o->r_max > 0 ? std::min<int64_t>(mn, o->r_max) : mn;
   if (cap > 1024)
@@ -195,6 +197,7 @@ inline svt_status make_params(int64_t m, int64_t n, const svt_options* o, Params
   if (t < 1) t = 1;
   P->m = m; P->n = n; P->r_cap = (int)cap; P->t_eff = (int)std::min<int64_t>(t, 1 << 20);
   P->dt = o->dt; P->np = o->n_power; P->power_steps = o->power_steps; P->recycle = o->recycle;
+  P->stop = o->stop;
   P->beta = o->beta; P->eps_thr0 = o->eps_thr0; P->seed = o->seed;
   return SVT_OK;
 }
@@ -304,8 +307,8 @@ struct Work {
     cudaStream_t s = nullptr;
     ~OwnedStream() { if (s) cudaStreamDestroy(s); }
   } cap;
-  // [0, 2 r_cap + kFlagWords) for the graph's copies, then 4 doubles for the caller
-  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + kFlagWords + 4; }
+  // [0, 2 r_cap + kFlagWords) for the graph's copies, then 8 doubles for the caller
+  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + kFlagWords + 8; }
   double* pin_tail() const { return host_pin + 2 * (size_t)P.r_cap + kFlagWords; }
 
   void layout(Arena& a) {

@@ -111,12 +111,47 @@ std::vector<cudaEvent_t> g_pool;
 
 namespace {
 
+// The evaluation set of svt_complete_eval on the device: its own sorted pattern, the
+// values in that pattern's CSR order, and a zero Y for the sampled pass (delta = 0).
+template <typename T>
+struct EvalSet {
+  int64_t n = 0;
+  svt_pattern* pat = nullptr;
+  DeviceBlock blk;
+  T* a = nullptr;
+  T* y = nullptr;
+  ~EvalSet() { if (pat) svt_pattern_destroy(pat); }
+  svt_status init(int64_t m, int64_t nc, int64_t ne, const int32_t* r, const int32_t* c,
+                  const T* v, cudaStream_t st) {
+    n = ne;
+    if (ne <= 0) return SVT_OK;
+    Arena a0;
+    a0.take<int32_t>(ne); a0.take<int32_t>(ne); a0.take<T>(ne); a0.take<T>(ne); a0.take<T>(ne);
+    SVT_TRY(blk.alloc(a0.off, st));
+    Arena b; b.base = (char*)blk.ptr;
+    int32_t* r2 = b.take<int32_t>(ne);
+    int32_t* c2 = b.take<int32_t>(ne);
+    T* v2 = b.take<T>(ne);
+    a = b.take<T>(ne);
+    y = b.take<T>(ne);
+    SVT_CUDA(cudaMemcpyAsync(r2, r, ne * sizeof(int32_t), cudaMemcpyDefault, st));
+    SVT_CUDA(cudaMemcpyAsync(c2, c, ne * sizeof(int32_t), cudaMemcpyDefault, st));
+    SVT_CUDA(cudaMemcpyAsync(v2, v, ne * sizeof(T), cudaMemcpyDefault, st));
+    SVT_TRY(build_pattern(m, nc, ne, r2, c2, st, &pat));
+    SVT_TRY((gather_convert<T, T>(ne, pat->csr_src, v2, a, st)));
+    SVT_CUDA(cudaMemsetAsync(y, 0, ne * sizeof(T), st));
+    return SVT_OK;
+  }
+};
+
 template <typename T>
 svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                          const int32_t* cols, const T* vals, double tau, double delta,
                          double tol, int32_t maxit, const svt_options* opt, double* Uo,
                          double* So, double* Vo, int32_t cap, svt_result* res,
-                         svt_iter_log* log, int32_t log_cap) {
+                         svt_iter_log* log, int32_t log_cap, int64_t n_eval = 0,
+                         const int32_t* eval_rows = nullptr, const int32_t* eval_cols = nullptr,
+                         const T* eval_vals = nullptr) {
   const auto t_start = clk::now();
   Params P;
   SVT_TRY(make_params(m, n, opt, &P));
@@ -151,6 +186,8 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   }
   struct PatGuard { svt_pattern* p; ~PatGuard() { svt_pattern_destroy(p); } } pg{pat};
   res->seconds_pattern = seconds_since(t_pat);
+  EvalSet<T> ev;
+  SVT_TRY(ev.init(m, n, n_eval, eval_rows, eval_cols, eval_vals, st));
 
   auto zero_outputs = [&]() -> svt_status {
     // X = 0: k = 0, outputs cleared
@@ -306,6 +343,11 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
       SVT_TRY(sampled_update<T>(pat, Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
                                 W.part, W.flags, st, true));
     }
+    if (ev.n > 0) {  // MAE of X^(i) = U[:, :k] W^T on the evaluation set (delta = 0: Y stays 0)
+      SVT_TRY(sampled_update<T>(ev.pat, Qnext, W.ldq, W.Wk, W.ldk, k, ev.a, ev.y, 0.0, W.dsc + 8,
+                                W.part, W.flags + 5, st, true));
+      SVT_CUDA(cudaMemcpyAsync(hsum + 4, W.dsc + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     SVT_CUDA(cudaMemcpyAsync(hsum, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaMemcpyAsync(hsum + 3, W.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaMemcpyAsync(reinterpret_cast<unsigned*>(hsum + 3) + 1, W.flags + 4, sizeof(unsigned),
@@ -343,11 +385,12 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
       L.iter = i; L.r = r; L.k = k; L.blocks = ro.blocks; L.cooled = cooled ? 1 : 0;
       L.exhausted = ro.exhausted ? 1 : 0; L.eps = ro.eps; L.eps_thr = thr_used;
       L.rel_residual = rel; L.mae = mae; L.sigma_max = r > 0 ? ro.sigma[0] : 0.0;
+      L.mae_eval = ev.n > 0 ? hsum[5] / (double)ev.n : std::nan("");
       L.seconds = seconds_since(t_it);
       res->log_len = i;
     }
     res->r = r;
-    if (rel < tol) { status = SVT_OK; break; }
+    if ((P.stop == SVT_STOP_MAE ? mae : rel) < tol) { status = SVT_OK; break; }
     if (!fused) {  // Y^(i+1) is in y_csr; refresh its CSC copy
       SVT_PROF("gather_csc", (double)nnz * (4 + 2 * sizeof(T)), st);
       SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
@@ -444,7 +487,7 @@ extern "C" void svt_default_options(svt_options* o) {
   o->power_steps = 100;
   o->precision = SVT_FP64;
   o->recycle = SVT_RECYCLE_ALL;
-  o->reserved = 0;
+  o->stop = SVT_STOP_RESIDUAL;
   o->beta = 0.95;
   o->eps_thr0 = 0.9;
   o->seed = 0x5EEDull;
@@ -596,6 +639,17 @@ extern "C" svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int3
                                    double tol, int32_t maxit, const svt_options* opt, double* U,
                                    double* S, double* V, int32_t cap, svt_result* res,
                                    svt_iter_log* log, int32_t log_cap) {
+  return svt_complete_eval(m, n, nnz, rows, cols, vals, 0, nullptr, nullptr, nullptr, tau, delta,
+                           tol, maxit, opt, U, S, V, cap, res, log, log_cap);
+}
+
+extern "C" svt_status svt_complete_eval(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                                        const int32_t* cols, const void* vals, int64_t n_eval,
+                                        const int32_t* eval_rows, const int32_t* eval_cols,
+                                        const void* eval_vals, double tau, double delta,
+                                        double tol, int32_t maxit, const svt_options* opt,
+                                        double* U, double* S, double* V, int32_t cap,
+                                        svt_result* res, svt_iter_log* log, int32_t log_cap) {
   using namespace svt;
   if (!res) return fail(SVT_ERR_ARG, "complete: null result");
   memset(res, 0, sizeof(*res));
@@ -606,13 +660,17 @@ extern "C" svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int3
   if (!(tau > 0.0) || !(delta > 0.0) || !std::isfinite(tau) || !std::isfinite(delta) || std::isnan(tol))
     return fail(SVT_ERR_ARG, "complete: need finite tau > 0, delta > 0");
   if (nnz > 0 && (!rows || !cols || !vals)) return fail(SVT_ERR_ARG, "complete: null input array");
+  if (n_eval < 0 || (n_eval > 0 && (!eval_rows || !eval_cols || !eval_vals)))
+    return fail(SVT_ERR_ARG, "complete: bad evaluation set");
   svt_status st;
   if (opt->precision == SVT_FP64)
     st = complete_impl<double>(m, n, nnz, rows, cols, (const double*)vals, tau, delta, tol, maxit,
-                               opt, U, S, V, cap, res, log, log_cap);
+                               opt, U, S, V, cap, res, log, log_cap, n_eval, eval_rows, eval_cols,
+                               (const double*)eval_vals);
   else if (opt->precision == SVT_MIXED_FP32)
     st = complete_impl<float>(m, n, nnz, rows, cols, (const float*)vals, tau, delta, tol, maxit,
-                              opt, U, S, V, cap, res, log, log_cap);
+                              opt, U, S, V, cap, res, log, log_cap, n_eval, eval_rows, eval_cols,
+                              (const float*)eval_vals);
   else
     st = fail(SVT_ERR_ARG, "complete: unknown precision");
   if (st < 0) {

@@ -19,6 +19,7 @@ def test_header_declares_the_boundary():
     names = L.header_functions()
     for required in ("svt_complete", "svt_r4svd", "svt_pattern_create", "svt_pattern_destroy",
                      "svt_spmm", "svt_sampled_update", "svt_sampled_update_recycle",
+                     "svt_complete_eval",
                      "svt_gaussian_block"):
         assert required in names
 
@@ -34,7 +35,7 @@ def test_every_header_symbol_is_exported(lib):
 def test_struct_layouts():
     # int32 fields first, then 8-byte fields, as declared in the header
     assert C.sizeof(L.Options) == 8 * 4 + 3 * 8 + 8
-    assert C.sizeof(L.IterLog) == 6 * 4 + 6 * 8
+    assert C.sizeof(L.IterLog) == 6 * 4 + 7 * 8
     assert C.sizeof(L.Result) == 6 * 4 + 6 * 8
 
 
@@ -43,7 +44,7 @@ def test_defaults_and_strings(lib):
     lib.svt_default_options(C.byref(o))
     assert (o.t, o.dt, o.n_power, o.r_max) == (-1, 10, 0, 0)
     assert abs(o.beta - 0.95) < 1e-15 and o.precision == L.SVT_FP64
-    assert (o.recycle, o.reserved) == (0, 0)
+    assert (o.recycle, o.stop) == (0, 0)
     assert lib.svt_abi_version() == 2
     assert lib.svt_status_string(L.SVT_ERR_DUPLICATE) == b"duplicate observed entry"
     assert lib.svt_status_string(12345) == b"unknown status"
@@ -62,13 +63,16 @@ def test_argument_validation_without_gpu(lib):
     assert b"tau" in lib.svt_last_error()
     h = C.c_void_p()
     assert lib.svt_pattern_create(-1, 3, 0, None, None, None, C.byref(h)) == L.SVT_ERR_ARG
-    for field, value in (("recycle", 3), ("reserved", 1)):
+    for field, value, word in (("recycle", 3, b"recycle"), ("stop", 2, b"stop")):
         bad = L.Options()
         lib.svt_default_options(C.byref(bad))
         setattr(bad, field, value)
         st = lib.svt_complete(4, 5, 0, None, None, None, 1.0, 1.0, 1e-3, 10, C.byref(bad), None,
                               None, None, 5, C.byref(res), None, 0)
-        assert st == L.SVT_ERR_ARG and b"recycle" in lib.svt_last_error()
+        assert st == L.SVT_ERR_ARG and word in lib.svt_last_error()
+    st = lib.svt_complete_eval(4, 5, 0, None, None, None, 3, None, None, None, 1.0, 1.0, 1e-3, 10,
+                               C.byref(o), None, None, None, 5, C.byref(res), None, 0)
+    assert st == L.SVT_ERR_ARG and b"evaluation" in lib.svt_last_error()
     sums = (C.c_double * 3)()
     assert lib.svt_sampled_update_recycle(None, L.SVT_FP64, None, 4, 4, None, 4, 2, None, None, 1.0,
                                           None, 4, sums, None) == L.SVT_ERR_ARG

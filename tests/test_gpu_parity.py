@@ -445,6 +445,34 @@ def test_complete_fp64_recycle_variants(svt, torch_mod, recycle, over):
     _assert_fp64_parity(w, ref, got)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_complete_mae_stop_and_evaluation_curve(svt, torch_mod, prec):
+    """Training-MAE stop rule and the held-out MAE of every iterate (Section 3.2) against
+    the oracle: the same stopping iteration and per-iteration held-out MAE."""
+    w = workloads.random_lowrank(240, 200, 5, 0.35, seed=29, n_hold=3000, maxit=300)
+    tol_mae = 0.05 * float(np.mean(np.abs(w.vals)))
+    ev = (w.held_rows, w.held_cols, w.held_vals)
+    kw = dict(t=w.t, dt=w.dt, beta=w.beta, eps_thr0=w.eps_thr0, r_max=w.r_max, seed=w.seed,
+              n_power=w.n_power, stop="mae")
+    ref = oracle.svt(w.m, w.n, w.rows, w.cols, w.vals, w.tau, w.delta, tol_mae, w.maxit,
+                     eval_set=ev, **kw)
+    vals = w.vals if prec == "fp64" else w.vals.astype(np.float32)
+    got = svt.complete(w.m, w.n, w.rows, w.cols, vals, w.tau, w.delta, tol_mae, w.maxit,
+                       precision=prec, eval_set=(ev[0], ev[1], ev[2] if prec == "fp64" else
+                                                 ev[2].astype(np.float32)), **kw)
+    assert ref.status == "ok" and 3 < ref.iters < w.maxit
+    me_ref = np.array([e["mae_eval"] for e in ref.log])
+    me_got = np.array([e["mae_eval"] for e in got.log])
+    if prec == "fp64":
+        assert got.iters == ref.iters
+        assert np.max(np.abs(me_got - me_ref) / me_ref) < 1e-9
+    else:
+        assert abs(got.iters - ref.iters) <= 1
+        n = min(got.iters, ref.iters)
+        assert np.max(np.abs(me_got[:n] - me_ref[:n]) / me_ref[:n]) < 1e-3
+    assert got.log[-1]["mae"] < tol_mae <= got.log[-2]["mae"]
+
+
 def test_complete_mixed_recycle_kept(svt, torch_mod):
     w = workloads.make("lowrank500")
     ref, got = _run_pair(svt, torch_mod, w, 40, "mixed", recycle="kept")

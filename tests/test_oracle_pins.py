@@ -281,6 +281,30 @@ def test_svt_recycling_variants():
         oracle.svt(m, n, rows, cols, M[rows, cols], 1.0, 1.2, 0.0, 2, recycle="some")
 
 
+def test_svt_mae_stop_rule_and_evaluation_curve():
+    """stop="mae" ends at the first iteration whose training MAE is below tol (Section 3);
+    the evaluation-set MAE of each iteration is the mean |A - X| of that iterate on the
+    held-out entries, here checked on the returned (last) iterate by a dense product."""
+    rng = np.random.default_rng(8)
+    m, n = 70, 60
+    M = rng.standard_normal((m, 3)) @ rng.standard_normal((3, n))
+    mask = rng.random((m, n)) < 0.5
+    rows, cols = np.nonzero(mask)
+    er, ec = np.nonzero(~mask)
+    res = oracle.svt(m, n, rows, cols, M[rows, cols], 5.0, 1.5, 0.05, 200, stop="mae",
+                     eval_set=(er, ec, M[er, ec]), seed=3)
+    maes = [e["mae"] for e in res.log]
+    assert res.status == "ok" and maes[-1] < 0.05 and all(v >= 0.05 for v in maes[:-1])
+    X = (res.U * res.S) @ res.V.T
+    assert math.isclose(res.log[-1]["mae_eval"], float(np.mean(np.abs(M[er, ec] - X[er, ec]))),
+                        rel_tol=1e-12)
+    assert math.isclose(res.log[-1]["mae"], float(np.mean(np.abs(M[rows, cols] - X[rows, cols]))),
+                        rel_tol=1e-12)
+    plain = oracle.svt(m, n, rows, cols, M[rows, cols], 5.0, 1.5, 0.05, 200, seed=3)
+    assert all(math.isnan(e["mae_eval"]) for e in plain.log)
+    assert plain.log[-1]["rel_residual"] < 0.05 <= plain.log[-2]["rel_residual"]
+
+
 def test_r4svd_rank_cap_and_exhaustion():
     rng = np.random.default_rng(23)
     # rank-3 matrix with a full pattern: the range is exhausted after 3 directions
