@@ -473,6 +473,23 @@ def test_complete_mae_stop_and_evaluation_curve(svt, torch_mod, prec):
     assert got.log[-1]["mae"] < tol_mae <= got.log[-2]["mae"]
 
 
+def test_complete_image1024_mae_stop(svt, torch_mod):
+    """The image shape of Section 3.1 at 1024 x 1024 (20% of the pixels, power-law
+    spectrum): revealed ranks grow to the 512 cap within 40 iterations, so the eigen start
+    runs in its large-r (global-memory Jacobi) form and the CSR-order update takes over
+    above 256 columns.  FP64 parity on the first 34 iterations under the training-MAE rule."""
+    w = workloads.make("image1024")
+    ref, got = _run_pair(svt, torch_mod, w, 34, "fp64", tol=1.0, stop="mae")
+    assert max(e["r"] for e in ref.log) > 256
+    assert got.iters == ref.iters and got.k == ref.k
+    assert [(e["r"], e["k"], e["blocks"]) for e in got.log] == [(e["r"], e["k"], e["blocks"]) for e in ref.log]
+    p = ref.pattern
+    x_ref = _completed(ref.U, ref.S, ref.V, p.csr_rows(), p.col_idx)
+    x_got = _completed(got.U, got.S, got.V, p.csr_rows(), p.col_idx)
+    print("image1024 relative difference", _rel(x_got, x_ref))
+    assert _rel(x_got, x_ref) < 1e-8
+
+
 def test_complete_mixed_recycle_kept(svt, torch_mod):
     w = workloads.make("lowrank500")
     ref, got = _run_pair(svt, torch_mod, w, 40, "mixed", recycle="kept")
