@@ -87,6 +87,7 @@ enum : unsigned {
   FLAG_NONFINITE = 4u,   // non-finite value met in a reduction
   FLAG_CHOLESKY = 8u,    // non-positive pivot in a small Cholesky factorisation
   FLAG_TC_TIMEOUT = 16u, // a bounded wait of the tensor-core lift ran out (result not written)
+  FLAG_GRID_TIMEOUT = 32u, // a grid barrier of the cooperative Jacobi ran out
 };
 
 // ---------------------------------------------------------------- scratch arena

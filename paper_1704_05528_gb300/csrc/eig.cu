@@ -18,6 +18,7 @@
 // The eigenpairs are finally sorted by descending eigenvalue.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 
@@ -28,6 +29,7 @@ namespace svt {
 namespace {
 
 constexpr int kJacThreads = 1024;
+constexpr int kJacGridThreads = 512;
 
 __device__ __forceinline__ void rr_pair(int step, int i, int N, int* p, int* q) {
   // circle method over N (even) players; player 0 fixed
@@ -521,6 +523,161 @@ size_t eig_scratch(int r) {
 }
 
 namespace {
+// Grid-wide barrier of a cooperative launch: an arrival count and a generation word in
+// global memory (zero before the launch).  Bounded: a wait that runs out returns false.
+__device__ bool grid_barrier(unsigned* bar, unsigned* gen_local) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok_s = 1;
+    const unsigned gen = *gen_local;
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {  // last to arrive: reset and release
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      const volatile unsigned* g = &bar[1];
+      unsigned spins = 0;
+      while (*g == gen) {
+        if (++spins > (1u << 24)) { ok_s = 0; break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *gen_local = gen + 1;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The binary32 cyclic Jacobi of jacobi_sweeps for r above what one CTA's shared memory
+// holds, spread over a cooperative grid.  A is double-buffered: a rotating step reads
+// A_src and writes every element of A_dst, so no CTA ever writes what another may still
+// be reading, and one grid barrier per rotating step suffices.  Every CTA computes the
+// step's rotations itself from A_src (the same values everywhere, hence the same rotations
+// and the same decision to skip a step that rotates nothing), and the 2 x 2 block updates
+// J_i^T A J_j of the step are divided over all threads of the grid, one block per thread:
+// each element gets the same operations in the same order as in the single-CTA kernel.
+// V is updated in place (each element belongs to one block of the step).  A and V live in
+// global memory and are read around L1 (other CTAs write them).  A barrier that runs out
+// raises FLAG_GRID_TIMEOUT in *status and every CTA stops.
+__global__ void __launch_bounds__(kJacGridThreads)
+k_jacobi32_grid(int r, const double* __restrict__ G, int64_t ldg, float* A, float* A2, float* V,
+                int max_sweeps, int* sweeps_out, unsigned* bar, unsigned* status) {
+  __shared__ float cs_c[512], cs_s[512];
+  __shared__ int pp[512], qq[512];
+  __shared__ float scale;
+  const int tid = threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  unsigned gen = 0;
+  for (int64_t t = gtid; t < (int64_t)r * r; t += gthreads) {
+    const int a = (int)(t / r), b = (int)(t - (t / r) * r);
+    __stcg(&A[t], (float)G[(int64_t)a * ldg + b]);
+    __stcg(&V[t], a == b ? 1.0f : 0.0f);
+  }
+  bool alive = grid_barrier(bar, &gen);
+  if (tid < 32) {
+    float mx = 0.f;
+    for (int i = tid; i < r; i += 32) mx = fmaxf(mx, fabsf(__ldcg(&A[(int64_t)i * r + i])));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (tid == 0) scale = mx;
+  }
+  __syncthreads();
+  const int N = (r + 1) & ~1;
+  const int npairs = N / 2;
+  float* src = A;
+  float* dst = A2;
+  int sweep = 0;
+  for (; sweep < max_sweeps && alive; ++sweep) {
+    int rotated = 0;
+    for (int step = 0; step < N - 1 && alive; ++step) {
+      int any = 0;
+      for (int i = tid; i < npairs; i += blockDim.x) {
+        int p, q;
+        rr_pair(step, i, N, &p, &q);
+        if (p > q) { const int t = p; p = q; q = t; }
+        float c = 1.f, sn = 0.f;
+        if (q < r) {
+          const float apq = __ldcg(&src[(int64_t)p * r + q]);
+          const float app = __ldcg(&src[(int64_t)p * r + p]), aqq = __ldcg(&src[(int64_t)q * r + q]);
+          if (jac_active(app, aqq, apq, scale)) {
+            const float theta = (aqq - app) / (2.f * apq);
+            float t;
+            if (fabsf(theta) > 1e15f) t = 0.5f / theta;
+            else t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+            c = rsqrtf(1.f + t * t);
+            sn = t * c;
+            any = 1;
+          }
+        }
+        cs_c[i] = c; cs_s[i] = sn; pp[i] = p; qq[i] = q;
+      }
+      // every CTA read the same A_src, so every CTA takes the same branch here
+      if (!__syncthreads_or(any)) continue;
+      rotated = 1;
+      for (int64_t t = gtid; t < (int64_t)npairs * npairs; t += gthreads) {
+        const int i = (int)(t / npairs), j = (int)(t - (t / npairs) * npairs);
+        const float ci = cs_c[i], si = cs_s[i], cj = cs_c[j], sj = cs_s[j];
+        const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
+        const bool hq_i = qi < r, hq_j = qj < r;
+        const float* a0 = src + (int64_t)pi * r;
+        const float* a1 = src + (int64_t)qi * r;
+        float* d0 = dst + (int64_t)pi * r;
+        float* d1 = dst + (int64_t)qi * r;
+        const float a00 = __ldcg(&a0[pj]);
+        const float a01 = hq_j ? __ldcg(&a0[qj]) : 0.f;
+        const float a10 = hq_i ? __ldcg(&a1[pj]) : 0.f;
+        const float a11 = (hq_i && hq_j) ? __ldcg(&a1[qj]) : 0.f;
+        if (si == 0.f && sj == 0.f) {  // no rotation touches this block: carry it over
+          __stcg(&d0[pj], a00);
+          if (hq_j) __stcg(&d0[qj], a01);
+          if (hq_i) __stcg(&d1[pj], a10);
+          if (hq_i && hq_j) __stcg(&d1[qj], a11);
+          continue;
+        }
+        const float b00 = ci * a00 - si * a10, b01 = ci * a01 - si * a11;
+        const float b10 = si * a00 + ci * a10, b11 = si * a01 + ci * a11;
+        __stcg(&d0[pj], cj * b00 - sj * b01);
+        if (hq_j) __stcg(&d0[qj], sj * b00 + cj * b01);
+        if (hq_i) __stcg(&d1[pj], cj * b10 - sj * b11);
+        if (hq_i && hq_j) __stcg(&d1[qj], sj * b10 + cj * b11);
+        if (sj != 0.f) {
+          float* v0 = V + (int64_t)pi * r;
+          float* v1 = V + (int64_t)qi * r;
+          const float v00 = __ldcg(&v0[pj]), v01 = __ldcg(&v0[qj]);
+          __stcg(&v0[pj], cj * v00 - sj * v01);
+          __stcg(&v0[qj], sj * v00 + cj * v01);
+          if (hq_i) {
+            const float v10 = __ldcg(&v1[pj]), v11 = __ldcg(&v1[qj]);
+            __stcg(&v1[pj], cj * v10 - sj * v11);
+            __stcg(&v1[qj], sj * v10 + cj * v11);
+          }
+        }
+      }
+      alive = grid_barrier(bar, &gen);
+      float* const t = src; src = dst; dst = t;
+    }
+    if (!rotated || !alive) break;
+    // would another sweep rotate anything?  (each CTA checks the whole of A_src, which no
+    // CTA writes before the next barrier: the same answer everywhere)
+    int more = 0;
+    for (int64_t t = tid; t < (int64_t)r * r && !more; t += blockDim.x) {
+      const int a = (int)(t / r), b = (int)(t - (t / r) * r);
+      if (a < b && jac_active(__ldcg(&src[(int64_t)a * r + a]), __ldcg(&src[(int64_t)b * r + b]),
+                              __ldcg(&src[t]), scale))
+        more = 1;
+    }
+    if (!__syncthreads_or(more)) {
+      ++sweep;
+      break;
+    }
+  }
+  if (!alive && tid == 0) atomicOr(status, FLAG_GRID_TIMEOUT);
+  if (blockIdx.x == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
 struct EigWork {
   float *A32, *V32;
   double *XP, *XPn, *CS, *E, *lam;
@@ -538,7 +695,7 @@ struct EigWork {
 }  // namespace
 
 svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
-                     int* sweeps_out) {
+                     int* sweeps_out, unsigned* status) {
   if (r <= 0) return SVT_OK;
   if (r > 1024) return fail(SVT_ERR_UNSUPPORTED, "eigensolver: r = %d exceeds 1024", r);
   const size_t rr = (size_t)r * r;
@@ -548,10 +705,32 @@ svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStre
   if (use_smem) {
     SVT_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
+    k_jacobi32<<<1, kJacThreads, smem, s>>>(r, G, ldg, w.A32, w.V32, 12, 1, sweeps_out);
+    SVT_LAUNCH_CHECK();
+  } else {
+    // above one CTA's shared memory: the cooperative grid version (one CTA per SM at most,
+    // and no more CTAs than 2 x 2 blocks of a step, r/2 squared, keep busy)
+    unsigned* bar = reinterpret_cast<unsigned*>(w.lam + r);
+    SVT_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    int per_sm = 0;
+    SVT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi32_grid, kJacGridThreads, 0));
+    if (per_sm < 1) return fail(SVT_ERR_UNSUPPORTED, "eigensolver: grid Jacobi does not fit an SM");
+    const int64_t work_items = ((int64_t)(r + 1) / 2) * ((r + 1) / 2);
+    const int64_t want = ceil_div(work_items, (int64_t)kJacGridThreads * 4);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, num_sms()));
+    int rr_ = r, sweeps = 12;
+    const double* G_ = G;
+    int64_t ldg_ = ldg;
+    float* A_ = w.A32;
+    float* A2_ = reinterpret_cast<float*>(w.XPn);  // free until the refinement
+    float* V_ = w.V32;
+    int* so = sweeps_out;
+    unsigned* st_ = status ? status : bar + 2;
+    void* args[] = {&rr_, &G_, &ldg_, &A_, &A2_, &V_, &sweeps, &so, &bar, &st_};
+    SVT_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi32_grid, dim3(blocks),
+                                         dim3(kJacGridThreads), args, 0, s));
+    count_launch();
   }
-  k_jacobi32<<<1, kJacThreads, use_smem ? smem : 0, s>>>(r, G, ldg, w.A32, w.V32, 12, use_smem,
-                                                         sweeps_out);
-  SVT_LAUNCH_CHECK();
   k_to_double_ld<<<(int)ceil_div((int64_t)rr, 256), 256, 0, s>>>(r, w.V32, w.XP, 2 * (int64_t)r);
   SVT_LAUNCH_CHECK();
   return SVT_OK;

@@ -99,7 +99,7 @@ svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub,
 // The two stages of sym_eig: binary32 Jacobi start (eigenvectors in work), then the
 // binary64 refinement and the sort.
 svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
-                     int* sweeps_out);
+                     int* sweeps_out, unsigned* status = nullptr);
 // Near-diagonal start for eig_refine (recycled bases): *status (device int) = 0 when the
 // start was written, 1 when a coupled cluster is too large (run eig_start instead; with
 // identity_on_fail the start is then the identity, so a refinement can follow unchecked).

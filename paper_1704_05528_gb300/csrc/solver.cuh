@@ -282,7 +282,7 @@ struct Work {
   double *coef = nullptr, *part = nullptr, *eigw = nullptr, *dsc = nullptr, *colss = nullptr;
   double *pv = nullptr, *pu = nullptr, *pw = nullptr;  // power-iteration vectors
   // status words: [0] FLAG bits, [1] cluster-start status, [2] Jacobi sweeps, [3] check
-  // status, [4] sticky FLAG_TC_TIMEOUT of the tensor-core lift
+  // status, [4] sticky FLAG_TC_TIMEOUT / FLAG_GRID_TIMEOUT (tensor-core lift, grid Jacobi)
   unsigned* flags = nullptr;
   float* tcb = nullptr;             // split U_B^T for the tensor-core lift (binary32 path)
   void* spmm_scr = nullptr;         // partial rows of the entry-chunked SpMM
@@ -452,7 +452,7 @@ svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram,
   if (!near_diagonal) {
     {
       SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
-      SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2)));
+      SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2), W.flags + 4));
     }
     SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
     SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
@@ -467,7 +467,9 @@ svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram,
   unsigned tc_status = 0;
   SVT_CUDA(cudaMemcpyAsync(&tc_status, W.flags + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   SVT_CUDA(cudaStreamSynchronize(st));
-  if (tc_status & FLAG_TC_TIMEOUT) return fail(SVT_ERR_CUDA, "tensor-core lift: a bounded wait ran out");
+  if (tc_status & (FLAG_TC_TIMEOUT | FLAG_GRID_TIMEOUT))
+    return fail(SVT_ERR_CUDA, "a bounded wait ran out (%s)",
+                (tc_status & FLAG_TC_TIMEOUT) ? "tensor-core lift" : "grid Jacobi");
   prof_flush();
   if (g_prof_on && !near_diagonal) {  // sweep count of the binary32 Jacobi stage (pseudo-entry)
     int sweeps = 0;
@@ -607,7 +609,9 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
       if (!(eps0 > eps_thr && s < P.r_cap)) {  // no new block: the graph's results stand
         unsigned fl[kFlagWords];
         memcpy(fl, hp + 2 * s, sizeof(fl));
-        if (fl[4] & FLAG_TC_TIMEOUT) return fail(SVT_ERR_CUDA, "tensor-core lift: a bounded wait ran out");
+        if (fl[4] & (FLAG_TC_TIMEOUT | FLAG_GRID_TIMEOUT))
+          return fail(SVT_ERR_CUDA, "a bounded wait ran out (%s)",
+                      (fl[4] & FLAG_TC_TIMEOUT) ? "tensor-core lift" : "grid Jacobi");
         o->r = s; o->blocks = 0; o->exhausted = false; o->eps = eps0; o->normB = normB;
         o->sigma.assign(s, 0.0);
         if (fl[1] == 0 && fl[3] == 0) {

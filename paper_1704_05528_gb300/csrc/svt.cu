@@ -370,7 +370,9 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     memcpy(sums, hsum, sizeof(sums));
     memcpy(&fl, hsum + 3, sizeof(unsigned));
     memcpy(&fl_tc, reinterpret_cast<const unsigned*>(hsum + 3) + 1, sizeof(unsigned));
-    if (fl_tc & FLAG_TC_TIMEOUT) return fail(SVT_ERR_CUDA, "tensor-core lift: a bounded wait ran out");
+    if (fl_tc & (FLAG_TC_TIMEOUT | FLAG_GRID_TIMEOUT))
+      return fail(SVT_ERR_CUDA, "a bounded wait ran out (%s)",
+                  (fl_tc & FLAG_TC_TIMEOUT) ? "tensor-core lift" : "grid Jacobi");
     rel = std::sqrt(sums[0]) / nA;
     mae = sums[1] / (double)nnz;
     if (!std::isfinite(rel) || (fl & FLAG_NONFINITE))
