@@ -45,7 +45,8 @@ typedef enum svt_status {
   SVT_ERR_ARG = -1,        /* invalid argument (sizes, parameters, capacities)      */
   SVT_ERR_INDEX = -2,      /* an observed index lies outside [0,m) x [0,n)          */
   SVT_ERR_DUPLICATE = -3,  /* an observed (row, col) pair occurs twice              */
-  SVT_ERR_CUDA = -4,       /* a CUDA runtime call failed                            */
+  SVT_ERR_CUDA = -4,       /* a CUDA runtime call failed, or a bounded device wait  */
+                           /* (tensor-core pipeline, grid barrier) ran out          */
   SVT_ERR_NUMERIC = -6,    /* non-finite input value, or a non-finite iterate       */
   SVT_ERR_UNSUPPORTED = -8 /* size beyond what this build supports                  */
 } svt_status;
