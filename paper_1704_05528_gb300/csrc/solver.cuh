@@ -307,9 +307,11 @@ struct Work {
     cudaStream_t s = nullptr;
     ~OwnedStream() { if (s) cudaStreamDestroy(s); }
   } cap;
-  // [0, 2 r_cap + kFlagWords) for the graph's copies, then 8 doubles for the caller
-  static size_t pin_doubles(int r_cap) { return 2 * (size_t)r_cap + kFlagWords + 8; }
+  // [0, 2 r_cap + kFlagWords) for the graph's copies, 8 doubles for the caller, then r_cap
+  // doubles staging the shrinkage coefficients of scaled_right
+  static size_t pin_doubles(int r_cap) { return 3 * (size_t)r_cap + kFlagWords + 8; }
   double* pin_tail() const { return host_pin + 2 * (size_t)P.r_cap + kFlagWords; }
+  double* pin_coef() const { return host_pin + 2 * (size_t)P.r_cap + kFlagWords + 8; }
 
   void layout(Arena& a) {
     const int64_t m = P.m, n = P.n, z = pat->nnz;
@@ -489,8 +491,8 @@ svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram,
 }
 
 // The eigen phase of a purely recycled basis, enqueued without host synchronisation so
-// that it can be captured: ||B||_F^2 by columns (copied to host_pin[0, r)), G = B B^T, the
-// near-diagonal cluster start (identity if a cluster is too large, status in flags[1]),
+// that it can be captured: G = B B^T (its diagonal, ||B||_F^2 by columns, copied to
+// host_pin[0, r)), the near-diagonal cluster start (identity if a cluster is too large, status in flags[1]),
 // the checked binary64 refinement (status in flags[3]), the status words and the
 // eigenvalues copied to host_pin, and U = Q U_B.
 template <typename T>
@@ -498,12 +500,13 @@ svt_status eig_phase_enqueue(Work<T>& W, T* Q, int r, T* Unew) {
   const int64_t m = W.P.m, n = W.P.n;
   const int sv = (int)sizeof(T);
   cudaStream_t st = W.s;
-  SVT_TRY(colsumsq<T>(n, r, W.Bt, W.ldb, W.colss, W.part, st));
-  SVT_CUDA(cudaMemcpyAsync(W.host_pin, W.colss, r * sizeof(double), cudaMemcpyDeviceToHost, st));
   {
     SVT_PROF("gram_B", gemm_bytes(n, r, 0, sv, false), st);
     SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
   }
+  // ||B||_F^2 by columns is the diagonal of G: one strided copy of G_cc to host_pin[0, r)
+  SVT_CUDA(cudaMemcpy2DAsync(W.host_pin, sizeof(double), W.G, (size_t)(r + 1) * sizeof(double),
+                             sizeof(double), (size_t)r, cudaMemcpyDeviceToHost, st));
   {
     SVT_PROF("eig_cluster", 8.0 * r * r, st);
     SVT_TRY(eig_start_clusters(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 1), true));
@@ -601,8 +604,7 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
     if (!ran) SVT_TRY(eig_phase_graph<T>(W, Q, s, Unew, &ran));
     if (ran) {
       have_normB = true;
-      SVT_CUDA(cudaStreamSynchronize(st));
-      prof_flush();
+      SVT_CUDA(cudaStreamSynchronize(st));  // (profiler events are folded in later, off this path)
       const double* hp = W.host_pin;
       for (int c = 0; c < s; ++c) normB += hp[c];
       const double eps0 = eps_of(normB);
@@ -726,7 +728,14 @@ template <typename T>
 svt_status scaled_right(Work<T>& W, int r, int k, const std::vector<double>& coef) {
   if (k <= 0) return SVT_OK;
   const int kp = (int)round_up(k, 4);
-  SVT_CUDA(cudaMemcpyAsync(W.coef, coef.data(), k * sizeof(double), cudaMemcpyHostToDevice, W.s));
+  // page-locked staging when available: the previous iteration's copy has completed (the
+  // caller waited for the update that follows it), so the buffer may be refilled
+  const double* src = coef.data();
+  if (W.host_pin && k <= W.P.r_cap) {
+    memcpy(W.pin_coef(), coef.data(), k * sizeof(double));
+    src = W.pin_coef();
+  }
+  SVT_CUDA(cudaMemcpyAsync(W.coef, src, k * sizeof(double), cudaMemcpyHostToDevice, W.s));
   const int64_t total = (int64_t)r * kp;
   k_scale_cols<T><<<(int)std::min<int64_t>(ceil_div(total, 256), 1024), 256, 0, W.s>>>(
       r, k, kp, W.Ub, r, W.coef, W.Tsm);
