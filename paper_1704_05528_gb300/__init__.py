@@ -174,16 +174,23 @@ def spmm(pattern: Pattern, y_csr, W, transpose=False, precision="fp64"):
 
 def spmm_noalloc(pattern: Pattern, y_csr, W, out, transpose=False, precision="fp64"):
     """Like spmm, but the library allocates nothing: its scratch is a fixed device array
-    (see svt_spmm_noalloc in the C header).  The caller supplies `out` (rows x w)."""
+    (see svt_spmm_noalloc in the C header).  The caller supplies `out` (rows x w).  W and
+    out are row-major with unit column stride; their leading dimensions are their row
+    strides, so either may be the first w columns of a wider array (a leading dimension
+    that is a multiple of 4 binary32 or 2 binary64 values lets the rows load as 16-byte
+    vectors)."""
     prec = _prec(precision)
     dt = _vdtype(prec)
     assert y_csr.is_cuda and y_csr.dtype == dt and y_csr.is_contiguous()
-    assert W.is_cuda and W.dtype == dt and W.is_contiguous() and W.dim() == 2
+    assert W.is_cuda and W.dtype == dt and W.dim() == 2 and W.stride(1) == 1
     w = W.shape[1]
     rows = pattern.n if transpose else pattern.m
-    assert out.is_cuda and out.dtype == dt and out.is_contiguous() and tuple(out.shape) == (rows, w)
+    assert out.is_cuda and out.dtype == dt and out.dim() == 2 and out.stride(1) == 1
+    assert tuple(out.shape) == (rows, w)
+    ldw = max(W.stride(0), w, 1) if W.shape[0] > 1 else max(w, 1)
+    ldo = max(out.stride(0), w, 1) if out.shape[0] > 1 else max(w, 1)
     _check(library().svt_spmm_noalloc(pattern.handle, prec, 1 if transpose else 0, _ptr(y_csr), _ptr(W),
-                                      max(w, 1), w, _ptr(out), max(w, 1), _stream_ptr()))
+                                      ldw, w, _ptr(out), ldo, _stream_ptr()))
     return out
 
 

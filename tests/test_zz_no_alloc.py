@@ -60,3 +60,24 @@ def test_noalloc_rejects_products_beyond_the_fixed_array(env):
         svt.spmm_noalloc(P, y, W, out, transpose=True)
     assert e.value.status == L.SVT_ERR_UNSUPPORTED
     assert b"fixed array" in svt.library().svt_last_error()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed", 2e-6)])
+def test_noalloc_takes_column_slices_of_wider_arrays(env, prec, tol):
+    """W and out may be the first w columns of wider row-major arrays: the binding passes
+    their row strides as leading dimensions, and the columns beyond w stay untouched."""
+    svt, torch = env
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rng = np.random.default_rng(9)
+    P = _pattern(svt, rng, 523, 347, 25000)
+    y = torch.from_numpy(rng.standard_normal(P.nnz)).to(device="cuda", dtype=dt)
+    for width, ld in ((10, 12), (7, 16), (3, 3)):
+        for transpose in (False, True):
+            rows_in, rows_out = (P.m, P.n) if transpose else (P.n, P.m)
+            Wb = torch.from_numpy(rng.standard_normal((rows_in, ld))).to(device="cuda", dtype=dt)
+            ref = svt.spmm(P, y, Wb[:, :width].contiguous(), transpose=transpose, precision=prec)
+            ob = torch.full((rows_out, ld + 2), float("nan"), device="cuda", dtype=dt)
+            svt.spmm_noalloc(P, y, Wb[:, :width], ob[:, :width], transpose=transpose, precision=prec)
+            err = (ob[:, :width] - ref).norm().item() / max(ref.norm().item(), 1e-300)
+            assert err <= tol
+            assert torch.isnan(ob[:, width:]).all()
