@@ -24,8 +24,8 @@ inline double seconds_since(clk::time_point t0) {
 }
 
 // ------------------------------------------------------------------ profiler
-// When enabled, each kernel class launched by the driver is bracketed by CUDA events
-// on the launching stream; elapsed times are folded in at the driver's sync points,
+// When enabled, each kernel class launched by the solver's host loop is bracketed by CUDA
+// events on the launching stream; elapsed times are folded in at the loop's sync points,
 // together with the algorithmic bytes that the class must move.
 struct ProfEntry {
   char name[32];
