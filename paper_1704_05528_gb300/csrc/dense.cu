@@ -41,13 +41,23 @@ __global__ void __launch_bounds__(256)
 k_gemm_tn_part(int64_t M, int p, int q, const TA* __restrict__ A, int64_t lda,
                const TB* __restrict__ B, int64_t ldb, int64_t rows_per_split,
                double* __restrict__ part, int symmetric) {
-  if (symmetric && blockIdx.x > blockIdx.y) return;   // lower tiles mirror upper ones
+  // A symmetric product (A == B) computes its upper tiles only (lower tiles mirror them):
+  // blockIdx.x then enumerates the tiles ta <= tb row by row, so that every CTA of the
+  // grid has work and the CTAs spread evenly over the SMs.
+  int ta = blockIdx.x, tb = blockIdx.y;
+  if (symmetric) {
+    const int T = (p + TN_TILE - 1) / TN_TILE;
+    int t = blockIdx.x;
+    ta = 0;
+    while (t >= T - ta) { t -= T - ta; ++ta; }
+    tb = ta + t;
+  }
   constexpr bool kF32 = sizeof(TA) == 4 && sizeof(TB) == 4;
   using TS = typename std::conditional<kF32, float, double>::type;
   __shared__ TS As[TN_TILE][TN_TILE + 1];
   __shared__ TS Bs[TN_TILE][TN_TILE + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int a0 = blockIdx.x * TN_TILE, b0 = blockIdx.y * TN_TILE;
+  const int a0 = ta * TN_TILE, b0 = tb * TN_TILE;
   const int64_t i_beg = (int64_t)blockIdx.z * rows_per_split;
   int64_t i_end = i_beg + rows_per_split;
   if (i_end > M) i_end = M;
@@ -363,8 +373,10 @@ svt_status gemm_tn(int64_t M, int p, int q, const TA* A, int64_t lda, const TB* 
   const int splits = tn_splits(M, p, q);
   const int64_t rows = round_up(ceil_div(M, splits), TN_TILE);
   const int used = (int)ceil_div(M, rows);
-  dim3 grid((unsigned)ceil_div(p, TN_TILE), (unsigned)ceil_div(q, TN_TILE), (unsigned)used);
   const int sym = (A == (const TA*)(const void*)B && p == q && lda == ldb) ? 1 : 0;
+  const int64_t tp = ceil_div(p, TN_TILE);
+  dim3 grid(sym ? (unsigned)(tp * (tp + 1) / 2) : (unsigned)tp,
+            sym ? 1u : (unsigned)ceil_div(q, TN_TILE), (unsigned)used);
   k_gemm_tn_part<TA, TB><<<grid, 256, 0, s>>>(M, p, q, A, lda, B, ldb, rows, part, sym);
   SVT_LAUNCH_CHECK();
   launch_reduce_parts(p, q, used, part, C, ldc, sym, s);
