@@ -82,6 +82,18 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(seconds, iters, device):
+    """Whole-job figures of N independent replicas: the slowest rank's time and the
+    iterations of all ranks (torch.distributed initialised, any backend)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    k = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(k, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(k[0])
+
+
 def make_workload(name, seed_offset=0):
     import workloads
     fn = workloads.WORKLOADS[name]
@@ -359,11 +371,7 @@ def our_arm(args):
     prof = svt.profile_read()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     if world > 1:
-        t = torch.tensor([elapsed, float(iters)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        elapsed, total_iters = float(tmax[0]), float(t[1])
+        elapsed, total_iters = reduce_over_ranks(elapsed, iters, "cuda")
     else:
         total_iters = float(iters)
     value = total_iters / elapsed
@@ -403,7 +411,11 @@ def our_arm(args):
     e2e_s = time.perf_counter() - t0
     h2d = int(w.nnz * (4 + 4 + (4 if prec == "mixed" else 8)))
     d2h = int(8 * (w.m * r_cap + r_cap + w.n * r_cap))
-    e2e_val = e2e_iters * world / e2e_s
+    if world > 1:
+        e2e_s, e2e_total = reduce_over_ranks(e2e_s, e2e_iters, "cuda")
+    else:
+        e2e_total = float(e2e_iters)
+    e2e_val = e2e_total / e2e_s
 
     # roofline of the dominant kernel class
     peaks, peak_src = load_peaks()
