@@ -32,10 +32,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SVT iterations/s (fast SVT with R4SVD)"
+# Time-to-tolerance legs run by default (workload:tol[:maxit]); see time_to_tol.
+TTT_DEFAULT = "lowrank500:1e-4:1500"
 UNIT = "iter/s"
 HBM_KERNELS = {"spmm_csr", "spmm_csc", "spmm_csc_recycled", "sampled_update", "update_recycled",
-               "gather_csc", "scatter_csr", "init_power", "lift_U", "lift_V", "gram_B",
-               "orthogonalise", "cholqr"}
+               "update_core", "update_fused", "gather_csc", "scatter_csr", "assemble_y", "init_power",
+               "lift_U", "lift_V", "gram_B", "orthogonalise", "cholqr"}
+# The fused sampled update runs as one kernel class on the gather path, or as two (the
+# sparse rest on the gather kernel, the dense core on the tensor cores) when the pattern has
+# a dense core; for the roofline the two are one step of the method.
+FUSED_PARTS = ("update_recycled", "update_core")
 
 
 def parse_args():
@@ -58,6 +64,9 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--eval", action="store_true",
                     help="log the held-out MAE of every iteration (an analysis run, not the headline)")
+    ap.add_argument("--ttt", default=TTT_DEFAULT,
+                    help="time-to-tolerance legs, comma separated workload:tol[:maxit] (mixed "
+                         "and binary64 solves to the stop rule); empty to skip")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -201,8 +210,10 @@ def flush_l2(buf):
 def narrow_spmm(svt, w, rows, cols, vals, prec, peaks, flush, width=10, reps=20):
     """The sampling product of a new block, X = Y Omega at the block width Delta t = 10
     (Algorithm 3), through the public API (svt_spmm_noalloc, CSR order).  Each sample is
-    one call between CUDA events after an L2 flush; the call synchronises, so a sample
-    also holds the enqueue latency.  The fastest of `reps` samples is reported."""
+    one call after an L2 flush.  Two times are reported: the library's CUDA events around
+    the product's kernels on the launching stream (the kernel time, averaged over the
+    samples), and events around the whole call (the fastest sample; the call waits for its
+    stream, so that time also holds the enqueue latency)."""
     import torch
     pat = svt.Pattern(w.m, w.n, rows, cols)
     try:
@@ -219,6 +230,8 @@ def narrow_spmm(svt, w, rows, cols, vals, prec, peaks, flush, width=10, reps=20)
         for _ in range(3):
             svt.spmm_noalloc(pat, y, Wv, ov, precision=prec)
         best = float("inf")
+        svt.profile_reset()
+        svt.profile_enable(True)
         for _ in range(reps):
             flush_l2(flush)
             e0.record(stream)
@@ -226,15 +239,91 @@ def narrow_spmm(svt, w, rows, cols, vals, prec, peaks, flush, width=10, reps=20)
             e1.record(stream)
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1))
+        svt.profile_enable(False)
+        pk = svt.profile_read().get("api_spmm_csr")
+        kern_ms = pk["ms"] / pk["launches"] if pk and pk["launches"] else None
         sv = 4 if prec == "mixed" else 8
         nbytes = w.nnz * (sv + 4) + 4 * (w.m + 1) + sv * width * (w.m + w.n)
-        gbs = nbytes / (best * 1e-3) / 1e9
-        return {"step": "X = Y Omega, CSR order", "w": width, "ms": best, "bytes": nbytes,
-                "GB/s": gbs, "frac_hbm": gbs / peaks["hbm_gbs"],
-                "timing": f"fastest of {reps} single calls after an L2 flush, CUDA events; "
-                          f"includes the call's enqueue latency"}
+        gbs = nbytes / (kern_ms * 1e-3) / 1e9 if kern_ms else None
+        call_gbs = nbytes / (best * 1e-3) / 1e9
+        return {"step": "X = Y Omega, CSR order", "w": width, "ms": kern_ms, "bytes": nbytes,
+                "GB/s": gbs, "frac_hbm": gbs / peaks["hbm_gbs"] if gbs else None,
+                "call_ms": best, "call_GB/s": call_gbs,
+                "timing": f"ms: mean over {reps} calls (L2 flushed before each) of the CUDA-event "
+                          f"time around the product's kernels; call_ms: fastest whole call, "
+                          f"enqueue latency included"}
     finally:
         pat.close()
+
+
+def time_to_tol(svt, spec, flush, reps=2):
+    """Wall time of a whole solve (pattern build, initialisation, iterations) until the
+    stop rule of Algorithm 4 holds, in mixed precision and in binary64, on the same
+    inputs resident in device memory: the fastest of `reps` solves, each after an L2
+    flush and between CUDA events.  The two completions are compared on the observed and
+    the held-out entries (the binary64 path agrees with the CPU oracle to 1e-9, which the
+    GPU tests check)."""
+    import torch
+    parts = spec.split(":")
+    name, tol = parts[0], float(parts[1])
+    w = make_workload(name)
+    maxit = int(parts[2]) if len(parts) > 2 else w.maxit
+    rows = torch.from_numpy(w.rows).cuda()
+    cols = torch.from_numpy(w.cols).cuda()
+    kw = dict(t=w.t, dt=w.dt, n_power=w.n_power, beta=w.beta, eps_thr0=w.eps_thr0, r_max=w.r_max,
+              seed=w.seed)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out, res = {}, {}
+    for prec in ("mixed", "fp64"):
+        v = torch.from_numpy(w.vals).to(device="cuda",
+                                        dtype=torch.float32 if prec == "mixed" else torch.float64)
+        svt.complete(w.m, w.n, rows, cols, v, w.tau, w.delta, tol, maxit, precision=prec, log=False, **kw)
+        best, r = float("inf"), None
+        for _ in range(reps):
+            flush_l2(flush)
+            e0.record(stream)
+            r = svt.complete(w.m, w.n, rows, cols, v, w.tau, w.delta, tol, maxit, precision=prec,
+                             log=False, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        res[prec] = r
+        out[prec] = {"seconds": best, "iters": r.iters, "converged": r.converged,
+                     "rel_residual": r.rel_residual, "k": r.k}
+
+    def completed(r, pr, pc):
+        pr = torch.from_numpy(pr).long().cuda()
+        pc = torch.from_numpy(pc).long().cuda()
+        U, S, V = r.U.double(), r.S.double(), r.V.double()
+        return ((U[pr] * S) * V[pc]).sum(dim=1)
+
+    def rel(a, b):
+        return float((a - b).norm() / b.norm()) if float(b.norm()) > 0 else float((a - b).norm())
+
+    m64, mix = res["fp64"], res["mixed"]
+    diff = {"observed": rel(completed(mix, w.rows, w.cols), completed(m64, w.rows, w.cols))}
+    if w.held_rows.size:
+        diff["held_out"] = rel(completed(mix, w.held_rows, w.held_cols),
+                               completed(m64, w.held_rows, w.held_cols))
+    return {"workload": w.name, "m": w.m, "n": w.n, "nnz_train": w.nnz, "tol": tol, "maxit": maxit,
+            "stop": "relative residual", "mixed": out["mixed"], "fp64": out["fp64"],
+            "speedup_mixed_over_fp64": out["fp64"]["seconds"] / out["mixed"]["seconds"],
+            "mixed_vs_fp64_rel_frobenius": diff,
+            "timing": f"fastest of {reps} whole solves per precision, L2 flushed, CUDA events"}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def oracle_sample(name, iters):
@@ -345,8 +434,7 @@ def our_arm(args):
 
     for _ in range(args.warmup):
         solve()
-    svt.profile_reset()
-    svt.profile_enable(True)
+    svt.profile_enable(False)  # the timed region runs unperturbed
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -367,9 +455,18 @@ def our_arm(args):
     barrier()
     clock_info = clocks.stop()
     kernel_launches = svt.launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    # per-kernel-class times from a separate pass of the same workload with the library's
+    # CUDA-event profiler on (it brackets each kernel class on its launching stream)
+    prof_steps = max(1, min(args.steps, 5))
+    svt.profile_reset()
+    svt.profile_enable(True)
+    for _ in range(prof_steps):
+        flush_l2(flush)
+        solve()
+    torch.cuda.synchronize()
     svt.profile_enable(False)
     prof = svt.profile_read()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
     if world > 1:
         elapsed, total_iters = reduce_over_ranks(elapsed, iters, "cuda")
     else:
@@ -382,12 +479,18 @@ def our_arm(args):
         vals64 = torch.from_numpy(w.vals).cuda()
         solve("fp64", vals64)
         barrier()
-        t0 = time.perf_counter()
+        flush_l2(flush)
+        ev0.record(stream)
         r64 = solve("fp64", vals64)
+        ev1.record(stream)
         torch.cuda.synchronize()
-        dt64 = time.perf_counter() - t0
+        dt64 = ev0.elapsed_time(ev1) / 1e3
         fp64_leg = {"iters_per_s": r64.iters / dt64, "iters": r64.iters, "seconds": dt64,
-                    "converged": r64.converged}
+                    "converged": r64.converged,
+                    "timing": "one solve after an untimed one, L2 flushed, CUDA events"}
+    ttt = None
+    if rank == 0 and args.ttt:
+        ttt = [time_to_tol(svt, spec, flush) for spec in args.ttt.split(",") if spec]
 
     # end to end through the C ABI with pinned host buffers (copies inside the region)
     rows_h = torch.from_numpy(w.rows).pin_memory()
@@ -423,10 +526,16 @@ def our_arm(args):
     events = {k: prof.pop(k)["launches"] for k in ("eig_start_oversize", "eig_start_rejected",
                                                    "eig_start_rejected_twice",
                                                    "eig_graph_unavailable") if k in prof}
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
+    classes = dict(prof)
+    if "update_core" in classes:  # one step: rest + core, per launch of the pair
+        parts = [classes.pop(k) for k in FUSED_PARTS if k in classes]
+        classes["update_fused"] = {"launches": max(p["launches"] for p in parts),
+                                   "ms": sum(p["ms"] for p in parts),
+                                   "bytes": sum(p["bytes"] for p in parts)}
+    dom = max(classes.items(), key=lambda kv: kv[1]["ms"])[0] if classes else None
     roofline = None
     if dom:
-        e = prof[dom]
+        e = classes[dom]
         per_launch_ms = e["ms"] / max(e["launches"], 1)
         per_launch_bytes = e["bytes"] / max(e["launches"], 1)
         if dom in HBM_KERNELS:
@@ -448,12 +557,18 @@ def our_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             cores = os.cpu_count() or 1
-            d = run_oracle_child(args.workload, 3, cores)
+            d = run_oracle_child(args.workload, 6, cores)
             timed = d["iter_seconds"][1:]
+            d1 = run_oracle_child(args.workload, 3, 1)
+            timed1 = d1["iter_seconds"][1:]
             cpu = {"value": len(timed) / sum(timed), "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"{args.workload}: SVT iterations 2-3 of one oracle solve, iteration "
+                   "sample": f"{args.workload}: SVT iterations 2-6 of one oracle solve, iteration "
                              f"time only (pattern build, initialisation, iteration 1 untimed), "
-                             f"binary64 numpy/scipy"}
+                             f"binary64 numpy/scipy with {cores} BLAS threads",
+                   "cpu_model": cpu_model(),
+                   "single_core": {"value": len(timed1) / sum(timed1), "unit": UNIT, "cores": 1,
+                                   "sample": f"{args.workload}: SVT iterations 2-3 of one oracle "
+                                             f"solve, one BLAS thread"}}
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {ex}"[:300]}
@@ -471,6 +586,8 @@ def our_arm(args):
                        "parallelism": f"replicas x{world}", "l2": "flushed (256 MiB write) before each step",
                        "iters_per_step": total_iters / world / args.steps},
             "time_to_tol_s": statistics.mean(conv_times) if conv_times else None,
+            "converges": bool(conv_times),
+            "time_to_tol": ttt,
             "eval": eval_summary(last_res) if ev_set is not None else None,
             "fp64_leg": fp64_leg,
             "gpu_launches": kernel_launches,

@@ -26,8 +26,11 @@
  *  - A call that fails returns a negative svt_status; svt_last_error() then gives a
  *    message for the calling thread.  No entry point terminates the process, and
  *    none leaves work running on the GPU when it returns.
- *  - The library allocates its own device scratch memory (stream-ordered); inputs
- *    and outputs are owned by the caller.
+ *  - Inputs and outputs are owned by the caller.  Device scratch memory of svt_complete,
+ *    svt_complete_eval and svt_r4svd comes from a caller-owned workspace when one is
+ *    passed (size from svt_workspace_size / svt_r4svd_workspace_size); with a NULL
+ *    workspace, and in the other entry points, the library takes stream-ordered
+ *    allocations from the device's default pool and returns them before the call ends.
  */
 #ifndef SVT_GB300_H
 #define SVT_GB300_H
@@ -87,6 +90,11 @@ typedef struct svt_options {
   int32_t precision;    /* svt_precision                                               */
   int32_t recycle;      /* svt_recycle (svt_complete)                                   */
   int32_t stop;         /* svt_stop (svt_complete)                                      */
+  int32_t core_rows;    /* SVT_MIXED_FP32 only: rows of the dense core of the fused update
+                           (the fullest rows, stored as a dense panel and updated on the
+                           tensor cores); -1 automatic (rows with at least n/10 observed
+                           entries, in whole tiles of 128), 0 none, > 0 that many rows    */
+  int32_t reserved;     /* zero                                                          */
   double beta;          /* cooling factor for the precision threshold (0 < beta < 1)   */
   double eps_thr0;      /* initial error-percentage threshold                          */
   uint64_t seed;        /* key of the counter-based Gaussian generator                 */
@@ -180,8 +188,11 @@ svt_status svt_spmm(const svt_pattern* p, int precision, int transpose, const vo
  * loads the library keeps the array until the process exits.  All calls share it and
  * its contents persist from call to call; nothing in it needs to start at zero, but
  * calls that overlap on the GPU race on it.  The first call on a device looks up the
- * array's address there and caches it; make that call before starting a stream
- * capture. */
+ * array's address there and caches it for the process, so a device reset
+ * (cudaDeviceReset) while the library is in use is not supported.  The call waits for
+ * its stream before returning, so it cannot be recorded into a stream capture.
+ * y_csr must hold the pattern's nnz values and W its n (transpose = 0) or m
+ * (transpose = 1) rows: the library cannot check buffer sizes. */
 svt_status svt_spmm_noalloc(const svt_pattern* p, int precision, int transpose,
                             const void* y_csr, const void* W, int64_t ldw, int32_t w, void* out,
                             int64_t ldo, void* stream);
@@ -215,6 +226,20 @@ svt_status svt_sampled_update_recycle(const svt_pattern* p, int precision, const
                                       int32_t k, const void* a_csc, void* y_csc, double delta,
                                       void* Bt, int64_t ldb, double* sums, void* stream);
 
+/* ------------------------------------------------------------------ workspaces */
+/* Device bytes that svt_complete / svt_complete_eval take from a caller workspace for a
+ * solve of an m x n matrix with nnz observed entries, n_eval evaluation entries (0 for
+ * svt_complete), output capacity cap and options opt (precision, rank cap, blocks,
+ * core_rows matter).  The figure covers the device copies of host inputs whether or not
+ * they will be needed, the sorted patterns and their sort scratch, the solver's arrays
+ * with the largest dense core the automatic choice could pick (at most 4096 rows), and
+ * the staging of host outputs; the solve itself uses at most this much.  0 for invalid
+ * arguments.  The workspace is caller-owned device memory, at least 256-byte aligned. */
+size_t svt_workspace_size(int64_t m, int64_t n, int64_t nnz, int64_t n_eval, int32_t cap,
+                          const svt_options* opt);
+/* Device bytes that svt_r4svd takes from a caller workspace (its work buffers). */
+size_t svt_r4svd_workspace_size(int64_t m, int64_t n, int64_t nnz, const svt_options* opt);
+
 /* ------------------------------------------------------------------ R4SVD */
 /* One call of R4SVD (Algorithm 3; Algorithm 2 when s == 0) on Y given in CSR order
  * on the pattern.  U_prev: m x s recycled left singular vectors (ld_prev), may be NULL
@@ -224,11 +249,15 @@ svt_status svt_sampled_update_recycle(const svt_pattern* p, int precision, const
  * Outputs (device, element type of y_csr): U (m x r, ldu) = Q U_B, V (n x r, ldv) the
  * right singular vectors, S[r] (binary64, host or device) the singular values in
  * descending order.  Capacities ldu, ldv and S must hold min(m, n, r_max) columns.
- * *r_out, *eps_out and *blocks_out are host pointers. */
+ * *r_out, *eps_out and *blocks_out are host pointers.  workspace (device, ws_bytes) may be
+ * NULL; otherwise the call allocates no device memory and takes its scratch from it, and
+ * a workspace smaller than svt_r4svd_workspace_size(m, n, nnz, opt) returns SVT_ERR_ARG
+ * before any work is queued.  The workspace must not be in use by other work meanwhile. */
 svt_status svt_r4svd(const svt_pattern* p, const void* y_csr, const void* U_prev,
                      int64_t ld_prev, int32_t s, double eps_thr, uint32_t iter,
                      const svt_options* opt, void* U, int64_t ldu, double* S, void* V,
-                     int64_t ldv, int32_t* r_out, double* eps_out, int32_t* blocks_out);
+                     int64_t ldv, int32_t* r_out, double* eps_out, int32_t* blocks_out,
+                     void* workspace, size_t ws_bytes);
 
 /* ------------------------------------------------------------------ fast SVT */
 /* Algorithm 4: complete the m x n matrix from nnz observed entries (rows, cols, vals).
@@ -240,26 +269,34 @@ svt_status svt_r4svd(const svt_pattern* p, const void* y_csr, const void* U_prev
  * Output X = U diag(S) V^T with U (m x cap), S[cap], V (n x cap), binary64, row-major,
  * host or device memory; the first res->k columns are valid.  cap must be at least
  * min(m, n, r_max).  log (host, may be NULL) receives up to log_cap iteration records.
- * res (host) is always written. */
+ * res (host) is always written.  workspace (device, ws_bytes) may be NULL: the solve then
+ * takes stream-ordered allocations.  Otherwise it allocates no device memory: every
+ * device array of the solve (input copies, patterns, iterates, the dense core) is carved
+ * from the workspace, and a workspace smaller than svt_workspace_size(m, n, nnz, 0, cap,
+ * opt) returns SVT_ERR_ARG before any work is queued.  Small page-locked host buffers
+ * for the solver's per-iteration reads are taken from a process-wide cache (allocated
+ * the first time a solve needs one, then reused).  The workspace must not be in use by
+ * other work meanwhile. */
 svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                         const int32_t* cols, const void* vals, double tau, double delta,
                         double tol, int32_t maxit, const svt_options* opt, double* U,
                         double* S, double* V, int32_t cap, svt_result* res,
-                        svt_iter_log* log, int32_t log_cap);
+                        svt_iter_log* log, int32_t log_cap, void* workspace, size_t ws_bytes);
 
 /* svt_complete with an evaluation set: n_eval entries (eval_rows, eval_cols, eval_vals;
  * host or device, element type of vals) that the solver never reads as data.  After each
  * iteration the mean absolute error of X^(i) on them goes to log[i].mae_eval: the
  * held-out ("testing set") MAE curve of Section 3.2.  The entries need not be disjoint
  * from Lambda, but must be distinct and in range (else SVT_ERR_DUPLICATE or
- * SVT_ERR_INDEX).  n_eval = 0 gives svt_complete. */
+ * SVT_ERR_INDEX).  n_eval = 0 gives svt_complete.  The workspace as in svt_complete, sized
+ * by svt_workspace_size(m, n, nnz, n_eval, cap, opt). */
 svt_status svt_complete_eval(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                              const int32_t* cols, const void* vals, int64_t n_eval,
                              const int32_t* eval_rows, const int32_t* eval_cols,
                              const void* eval_vals, double tau, double delta, double tol,
                              int32_t maxit, const svt_options* opt, double* U, double* S,
                              double* V, int32_t cap, svt_result* res, svt_iter_log* log,
-                             int32_t log_cap);
+                             int32_t log_cap, void* workspace, size_t ws_bytes);
 
 /* ------------------------------------------------------------------ unrolled SVT */
 typedef struct svt_unrolled_params {
@@ -325,6 +362,31 @@ void svt_unrolled_default_params(svt_unrolled_params* p, int precision);
  * the pattern errors of svt_pattern_create for either index set, SVT_ERR_NUMERIC
  * (non-finite iterate or CG residual, basis breakdown), SVT_ERR_UNSUPPORTED (see above
  * and svt_complete's rank cap), SVT_ERR_CUDA. */
+/* The same computation split for reverse-mode automatic differentiation.  The forward
+ * pass runs the T iterations, writes X^(T) on the held-out entries (x_held[nheld],
+ * binary64, caller order, host or device) and, when tape is not NULL, returns in *tape the
+ * state the reverse pass replays: the checkpoints every checkpoint_every iterations, the
+ * patterns and the last iterate, all in device memory owned by the tape (about
+ * (T / checkpoint_every + 3 checkpoint_every) copies of Y and of the basis).  With tape
+ * NULL only the forward runs and nothing is kept.  Arguments and errors as in
+ * svt_unrolled_grad; held-out values are not needed (the loss is the caller's). */
+typedef struct svt_unrolled_tape svt_unrolled_tape;
+svt_status svt_unrolled_forward(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                                const int32_t* cols, const void* vals, int64_t nheld,
+                                const int32_t* held_rows, const int32_t* held_cols, double tau,
+                                double delta, const svt_unrolled_params* p,
+                                const svt_options* opt, double* x_held, svt_unrolled_info* info,
+                                svt_unrolled_tape** tape);
+/* Reverse pass: given g_held[nheld] = dL/dX^(T) on the held-out entries (binary64, caller
+ * order, host or device), writes grad_vals[nnz] = dL/dvals (caller order, binary64, host
+ * or device, may be NULL) and grad_tau_delta[2] = {dL/dtau, dL/ddelta} (host or device, may
+ * be NULL).  Runs on the stream of the forward call; a tape serves one backward call
+ * (SVT_ERR_ARG on a second). */
+svt_status svt_unrolled_backward(svt_unrolled_tape* tape, const double* g_held, double* grad_vals,
+                                 double* grad_tau_delta, svt_unrolled_info* info);
+/* Releases the tape's device memory (after waiting for its stream). */
+void svt_unrolled_tape_destroy(svt_unrolled_tape* tape);
+
 svt_status svt_unrolled_grad(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                              const int32_t* cols, const void* vals, int64_t nheld,
                              const int32_t* held_rows, const int32_t* held_cols,
@@ -345,6 +407,17 @@ void svt_profile_reset(void);
 int svt_profile_read(int cap, char* names, int64_t* launches, double* ms, double* bytes);
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t svt_launch_count(void);
+
+/* ------------------------------------------------------------------ testing hook */
+/* Failure detection (no counterpart in the paper).  The cooperative-grid Jacobi used for
+ * revealed ranks above what one CTA's shared memory holds waits at a grid barrier after
+ * every rotating step; each wait gives up after a bounded number of polls (2^24 by
+ * default, about a second), sets a status flag and ends the kernel, and the solver then
+ * returns SVT_ERR_CUDA with a message naming the grid Jacobi.  This call sets that bound
+ * for later launches in the process (values below 1 count as 1) and returns the previous
+ * one, so that a test can make a wait run out and check that the error is reported and
+ * the device stays usable.  Not thread-safe with respect to solves running meanwhile. */
+unsigned svt_test_set_grid_wait_limit(unsigned polls);
 
 #ifdef __cplusplus
 }

@@ -15,6 +15,7 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["SVTError", "options", "Pattern", "gaussian_block", "spmm", "spmm_noalloc", "sampled_update",
+           "workspace_size", "r4svd_workspace_size",
            "sampled_update_recycle",
            "r4svd", "complete", "library", "launch_count", "profile_enable", "profile_reset", "profile_read",
            "unrolled_grad", "unrolled_params", "SVTUnrolled", "FP64", "MIXED_FP32"]
@@ -157,6 +158,17 @@ def gaussian_block(seed, it, block, n, w):
     return out
 
 
+def _check_spmm_operands(pattern, y, W, transpose):
+    """The C entry points cannot see buffer sizes: a short y or W would make the kernels
+    read past its end, so the sizes are checked here, before any work is queued."""
+    if y.dim() != 1 or y.numel() != pattern.nnz:
+        raise ValueError(f"y_csr must hold the pattern's {pattern.nnz} values, got shape {tuple(y.shape)}")
+    rows_in = pattern.m if transpose else pattern.n
+    if W.dim() != 2 or W.shape[0] != rows_in:
+        raise ValueError(f"W must have {rows_in} rows ({'m' if transpose else 'n'}), got shape "
+                         f"{tuple(W.shape)}")
+
+
 def spmm(pattern: Pattern, y_csr, W, transpose=False, precision="fp64"):
     """Y W (transpose False, W n x w) or Y^T W (transpose True, W m x w)."""
     torch = _torch()
@@ -164,6 +176,7 @@ def spmm(pattern: Pattern, y_csr, W, transpose=False, precision="fp64"):
     dt = _vdtype(prec)
     y = y_csr.to(device="cuda", dtype=dt).contiguous()
     W = W.to(device="cuda", dtype=dt).contiguous()
+    _check_spmm_operands(pattern, y, W, transpose)
     w = W.shape[1]
     rows = pattern.n if transpose else pattern.m
     out = torch.empty((rows, w), device="cuda", dtype=dt)
@@ -183,6 +196,7 @@ def spmm_noalloc(pattern: Pattern, y_csr, W, out, transpose=False, precision="fp
     dt = _vdtype(prec)
     assert y_csr.is_cuda and y_csr.dtype == dt and y_csr.is_contiguous()
     assert W.is_cuda and W.dtype == dt and W.dim() == 2 and W.stride(1) == 1
+    _check_spmm_operands(pattern, y_csr, W, transpose)
     w = W.shape[1]
     rows = pattern.n if transpose else pattern.m
     assert out.is_cuda and out.dtype == dt and out.dim() == 2 and out.stride(1) == 1
@@ -235,8 +249,32 @@ def sampled_update_recycle(pattern: Pattern, U, W, a_csc, y_csc, delta, precisio
     return Bt, tuple(sums)
 
 
-def r4svd(pattern: Pattern, y_csr, eps_thr, it, U_prev=None, precision="fp64", **kw):
-    """One R4SVD call (Algorithm 3; Algorithm 2 when U_prev is None)."""
+def _ws_args(workspace):
+    """(pointer, bytes) of a caller workspace: a CUDA tensor (any dtype, contiguous), or None."""
+    if workspace is None:
+        return C.c_void_p(0), 0
+    assert workspace.is_cuda and workspace.is_contiguous()
+    return C.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+
+
+def workspace_size(m, n, nnz, n_eval=0, cap=None, precision="fp64", **kw):
+    """Device bytes a solve (complete) takes from a caller workspace (svt_workspace_size)."""
+    o = options(precision, **kw)
+    if cap is None:
+        cap = min(m, n, o.r_max) if o.r_max > 0 else min(m, n)
+    return int(library().svt_workspace_size(m, n, nnz, n_eval, cap, C.byref(o)))
+
+
+def r4svd_workspace_size(m, n, nnz, precision="fp64", **kw):
+    """Device bytes an r4svd call takes from a caller workspace."""
+    o = options(precision, **kw)
+    return int(library().svt_r4svd_workspace_size(m, n, nnz, C.byref(o)))
+
+
+def r4svd(pattern: Pattern, y_csr, eps_thr, it, U_prev=None, precision="fp64", workspace=None, **kw):
+    """One R4SVD call (Algorithm 3; Algorithm 2 when U_prev is None).  workspace: a CUDA
+    tensor of at least r4svd_workspace_size bytes, from which the call takes its scratch
+    instead of allocating."""
     torch = _torch()
     o = options(precision, **kw)
     o.stream = _stream_ptr().value
@@ -252,7 +290,7 @@ def r4svd(pattern: Pattern, y_csr, eps_thr, it, U_prev=None, precision="fp64", *
     r, eps, blocks = C.c_int32(0), C.c_double(0), C.c_int32(0)
     _check(library().svt_r4svd(pattern.handle, _ptr(y), _ptr(Up), max(s, 1), s, float(eps_thr),
                                int(it) & 0xFFFFFFFF, C.byref(o), _ptr(U), r_cap, _ptr(S), _ptr(V), r_cap,
-                               C.byref(r), C.byref(eps), C.byref(blocks)))
+                               C.byref(r), C.byref(eps), C.byref(blocks), *_ws_args(workspace)))
     rr = r.value
     return dict(U=U[:, :rr], S=S[:rr], V=V[:, :rr], r=rr, eps=eps.value, blocks=blocks.value)
 
@@ -312,14 +350,15 @@ def _log_list(buf, n):
 
 
 def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", log=True,
-             on_host=None, eval_set=None, **kw) -> Completion:
+             on_host=None, eval_set=None, workspace=None, **kw) -> Completion:
     """Algorithm 4 on (rows, cols, vals).
 
     Host inputs (numpy) are copied to the device inside the call and the factors come
     back as numpy arrays; device inputs (torch CUDA tensors) give device outputs.
     eval_set = (rows, cols, vals) of held-out entries adds their MAE after every
     iteration to the log ("mae_eval"); stop="mae" ends on the training MAE instead of the
-    relative residual.
+    relative residual.  workspace: a CUDA tensor of at least workspace_size(...) bytes from
+    which the solve takes every device array instead of allocating.
     """
     torch = _torch()
     o = options(precision, **kw)
@@ -374,7 +413,7 @@ def complete(m, n, rows, cols, vals, tau, delta, tol, maxit, precision="fp64", l
         n_eval = keep_eval[0].shape[0]
     st = library().svt_complete_eval(m, n, nnz, *args, n_eval, *eval_args, float(tau), float(delta),
                                      float(tol), int(maxit), C.byref(o), *outs, r_cap, C.byref(res),
-                                     logbuf, log_cap)
+                                     logbuf, log_cap, *_ws_args(workspace))
     del keep, keep_eval
     _check(st)
     k = res.k
@@ -433,30 +472,95 @@ def unrolled_grad(m, n, rows, cols, vals, held_rows, held_cols, held_vals, tau, 
                 x_held=xh, info={k: getattr(info, k) for k in keys})
 
 
+class _Tape:
+    """Owner of a C-side unrolled tape (released when the Python object goes away)."""
+
+    def __init__(self, handle, nnz, nheld):
+        self.handle, self.nnz, self.nheld = handle, nnz, nheld
+
+    def release(self):
+        if self.handle is not None and self.handle.value:
+            library().svt_unrolled_tape_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def _host_or_device_ptr(x, dtype):
+    """(pointer, keep-alive) of a numpy array or torch tensor with the given numpy dtype."""
+    if isinstance(x, np.ndarray):
+        a = np.ascontiguousarray(x, dtype=dtype)
+        return a.ctypes.data_as(C.c_void_p), a
+    t = x.detach().contiguous()
+    return C.c_void_p(t.data_ptr()), t
+
+
 def _make_unrolled_function():
     torch = _torch()
 
     class SVTUnrolled(torch.autograd.Function):
-        """Held-out MSE of unrolled SVT as a differentiable function of the observed
-        values, tau and delta; backward returns the gradients from the hand-written
-        adjoint (svt_unrolled_grad), scaled by the incoming gradient."""
+        """X^(T) of unrolled SVT on the held-out entries, as a differentiable function of the
+        observed values, tau and delta.  forward runs svt_unrolled_forward on the device
+        (vals may be a CUDA tensor; nothing is copied through the host) and keeps the
+        checkpoint tape only when a gradient may be needed; backward hands the incoming
+        gradient on the predictions to svt_unrolled_backward, which replays the tape.
+        problem: m, n, rows, cols, held_rows, held_cols (numpy or CUDA int32), steps and
+        options (keywords of unrolled_grad)."""
 
         @staticmethod
         def forward(ctx, vals, tau, delta, problem):
-            res = unrolled_grad(problem["m"], problem["n"], problem["rows"], problem["cols"],
-                                vals.detach().cpu().numpy(), problem["held_rows"], problem["held_cols"],
-                                problem["held_vals"], float(tau), float(delta), problem["steps"],
-                                **problem.get("options", {}))
-            ctx.save_for_backward(torch.from_numpy(res["grad_vals"]).to(vals.dtype),
-                                  torch.tensor(res["grad_tau"], dtype=torch.float64),
-                                  torch.tensor(res["grad_delta"], dtype=torch.float64))
-            ctx.info = res["info"]
-            return torch.tensor(res["loss"], dtype=torch.float64)
+            opts = dict(problem.get("options", {}))
+            prec = opts.get("precision", "fp64")
+            up = unrolled_params(prec, steps=int(problem["steps"]),
+                                 **{k: opts.pop(k) for k in list(opts) if k in _UNROLLED_KEYS})
+            o = options(**opts)
+            o.stream = _stream_ptr().value
+            want = torch.float64 if o.precision == FP64 else torch.float32
+            v = vals.detach().to(want).contiguous()
+            r, kr = _host_or_device_ptr(problem["rows"], np.int32)
+            c, kc = _host_or_device_ptr(problem["cols"], np.int32)
+            hr, khr = _host_or_device_ptr(problem["held_rows"], np.int32)
+            hc, khc = _host_or_device_ptr(problem["held_cols"], np.int32)
+            nnz, nh = v.numel(), int(khr.shape[0])
+            x = torch.empty(nh, dtype=torch.float64, device=vals.device)
+            need = any(ctx.needs_input_grad[:3])
+            h = C.c_void_p()
+            info = L.UnrolledInfo()
+            _check(library().svt_unrolled_forward(problem["m"], problem["n"], nnz, r, c, C.c_void_p(v.data_ptr()),
+                                                  nh, hr, hc, float(tau), float(delta), C.byref(up),
+                                                  C.byref(o), C.c_void_p(x.data_ptr()), C.byref(info),
+                                                  C.byref(h) if need else None))
+            del kr, kc, khr, khc
+            ctx.tape = _Tape(h, nnz, nh) if need else None
+            ctx.info = {f[0]: getattr(info, f[0]) for f in L.UnrolledInfo._fields_}
+            ctx.vals_meta = (vals.dtype, vals.device)
+            ctx.scalar_meta = [(t.dtype, t.device) if torch.is_tensor(t) else None for t in (tau, delta)]
+            return x
 
         @staticmethod
         def backward(ctx, g):
-            gv, gt, gd = ctx.saved_tensors
-            return g * gv, (g * gt).to(torch.float64), (g * gd).to(torch.float64), None
+            tape = ctx.tape
+            if tape is None:
+                return None, None, None, None
+            dtype, device = ctx.vals_meta
+            gx = g.detach().to(device=device, dtype=torch.float64).contiguous()
+            grad = torch.empty(tape.nnz, dtype=torch.float64, device=device)
+            gtd = torch.empty(2, dtype=torch.float64, device=device)
+            info = L.UnrolledInfo()
+            try:
+                _check(library().svt_unrolled_backward(tape.handle, C.c_void_p(gx.data_ptr()),
+                                                       C.c_void_p(grad.data_ptr()), C.c_void_p(gtd.data_ptr()),
+                                                       C.byref(info)))
+            finally:
+                tape.release()
+            ctx.info = {f[0]: getattr(info, f[0]) for f in L.UnrolledInfo._fields_}
+            gs = [None if meta is None else gtd[i].to(dtype=meta[0], device=meta[1])
+                  for i, meta in enumerate(ctx.scalar_meta)]
+            return grad.to(dtype), gs[0], gs[1], None
 
     return SVTUnrolled
 

@@ -19,7 +19,8 @@ SVT_FP64, SVT_MIXED_FP32 = 0, 1
 class Options(C.Structure):
     _fields_ = [("t", C.c_int32), ("dt", C.c_int32), ("n_power", C.c_int32),
                 ("r_max", C.c_int32), ("power_steps", C.c_int32), ("precision", C.c_int32),
-                ("recycle", C.c_int32), ("stop", C.c_int32), ("beta", C.c_double), ("eps_thr0", C.c_double), ("seed", C.c_uint64),
+                ("recycle", C.c_int32), ("stop", C.c_int32), ("core_rows", C.c_int32),
+                ("reserved", C.c_int32), ("beta", C.c_double), ("eps_thr0", C.c_double), ("seed", C.c_uint64),
                 ("stream", C.c_void_p)]
 
 
@@ -70,7 +71,9 @@ SIGNATURES = {
     "svt_sampled_update_recycle": (C.c_int, [_P, C.c_int, _P, _I64, _I32, _P, _I64, _I32, _P, _P,
                                              _D, _P, _I64, _PD, _P]),
     "svt_r4svd": (C.c_int, [_P, _P, _P, _I64, _I32, _D, _U32, C.POINTER(Options), _P, _I64, _P,
-                            _P, _I64, _PI32, _PD, _PI32]),
+                            _P, _I64, _PI32, _PD, _PI32, _P, C.c_size_t]),
+    "svt_workspace_size": (C.c_size_t, [_I64, _I64, _I64, _I64, _I32, C.POINTER(Options)]),
+    "svt_r4svd_workspace_size": (C.c_size_t, [_I64, _I64, _I64, C.POINTER(Options)]),
     "svt_profile_enable": (None, [C.c_int]),
     "svt_profile_reset": (None, []),
     "svt_launch_count": (C.c_int64, []),
@@ -81,10 +84,16 @@ SIGNATURES = {
                                      C.POINTER(UnrolledInfo)]),
     "svt_complete": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _D, _D, _D, _I32,
                                C.POINTER(Options), _P, _P, _P, _I32, C.POINTER(Result),
-                               C.POINTER(IterLog), _I32]),
+                               C.POINTER(IterLog), _I32, _P, C.c_size_t]),
     "svt_complete_eval": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _I64, _P, _P, _P, _D, _D, _D, _I32,
                                     C.POINTER(Options), _P, _P, _P, _I32, C.POINTER(Result),
-                                    C.POINTER(IterLog), _I32]),
+                                    C.POINTER(IterLog), _I32, _P, C.c_size_t]),
+    "svt_test_set_grid_wait_limit": (C.c_uint, [C.c_uint]),
+    "svt_unrolled_forward": (C.c_int, [_I64, _I64, _I64, _P, _P, _P, _I64, _P, _P, _D, _D,
+                                        C.POINTER(UnrolledParams), C.POINTER(Options), _P,
+                                        C.POINTER(UnrolledInfo), C.POINTER(_P)]),
+    "svt_unrolled_backward": (C.c_int, [_P, _P, _P, _P, C.POINTER(UnrolledInfo)]),
+    "svt_unrolled_tape_destroy": (None, [_P]),
 }
 
 

@@ -551,107 +551,30 @@ svt_status upload_idx(const int32_t* src, int64_t count, int32_t* dst, cudaStrea
   return SVT_OK;
 }
 
+// Unrolled SVT as a tape: forward() runs the T iterations and keeps the checkpoints,
+// backward() replays them in reverse for a given gradient on the held-out predictions.
 template <typename T>
-svt_status unrolled_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
-                         const void* vals, int64_t nh, const int32_t* hrows, const int32_t* hcols,
-                         const void* hvals, double tau, double delta, const svt_unrolled_params& UP,
-                         const svt_options* opt, double* grad_vals, double* x_held, double* out3,
-                         svt_unrolled_info* info) {
-  const auto t0 = std::chrono::steady_clock::now();
-  Params P;
-  SVT_TRY(make_params(m, n, opt, &P));
-  cudaStream_t st = (cudaStream_t)opt->stream;
-  const int steps = UP.steps, ckpt = UP.checkpoint_every;
-  const double cg_tol = UP.cg_tol;
-  const int cg_maxit = UP.cg_maxit;
+struct UnrolledTape {
+  int64_t m = 0, n = 0, nnz = 0, nh = 0;
+  double tau = 0, delta = 0;
+  svt_unrolled_params UP{};
+  Params P{};
+  cudaStream_t st = nullptr;
+  bool dbl_in = false;
+  std::chrono::steady_clock::time_point t0;
   RitzStats ritz;
-  // index arrays on the device
-  DeviceBlock idx_blk;
-  Arena ia;
-  ia.take<int32_t>(nnz); ia.take<int32_t>(nnz); ia.take<int32_t>(nh); ia.take<int32_t>(nh);
-  SVT_TRY(idx_blk.alloc(ia.off, st));
-  Arena ib; ib.base = (char*)idx_blk.ptr;
-  int32_t* d_rows = ib.take<int32_t>(nnz);
-  int32_t* d_cols = ib.take<int32_t>(nnz);
-  int32_t* d_hrows = ib.take<int32_t>(nh);
-  int32_t* d_hcols = ib.take<int32_t>(nh);
-  SVT_TRY(upload_idx<T>(rows, nnz, d_rows, st));
-  SVT_TRY(upload_idx<T>(cols, nnz, d_cols, st));
-  SVT_TRY(upload_idx<T>(hrows, nh, d_hrows, st));
-  SVT_TRY(upload_idx<T>(hcols, nh, d_hcols, st));
+  CgStats cg;
+  DeviceBlock idx_blk, wb, t1, t2;
   svt_pattern* pl = nullptr;
   svt_pattern* ph = nullptr;
-  SVT_TRY(build_pattern(m, n, nnz, d_rows, d_cols, st, &pl));
-  struct G1 { svt_pattern* p; ~G1() { svt_pattern_destroy(p); } } g1{pl};
-  SVT_TRY(build_pattern(m, n, nh, d_hrows, d_hcols, st, &ph));
-  struct G2 { svt_pattern* p; ~G2() { svt_pattern_destroy(p); } } g2{ph};
-  if (nnz == 0 || nh == 0) return fail(SVT_ERR_ARG, "unrolled: need observed and held-out entries");
-
   Work<T> W;
-  W.P = P; W.pat = pl; W.s = st;
   AdjWork<T> A;
-  A.m = m; A.n = n; A.zl = nnz; A.zmax = std::max(nnz, nh); A.kcap = P.r_cap;
-  const int nck = (steps + ckpt - 1) / ckpt;
-  const int64_t ldq0 = ld_of(P.r_cap);
-  auto layout_all = [&](Arena& a, T** a_csr, T** y_csr, T** hv, T** xh, T** gH, T** ybar, T** abar,
-                        T** tmpz, T** ck_y, T** ck_Q, T** sg_y, T** sg_yc, T** sg_d, T** sg_U,
-                        T** sg_V, T** fin_V, T** vals_in, T** hvals_in, double** part3) {
-    *a_csr = a.take<T>(nnz); *y_csr = a.take<T>(nnz);
-    *hv = a.take<T>(nh); *xh = a.take<T>(nh); *gH = a.take<T>(nh);
-    *ybar = a.take<T>(nnz); *abar = a.take<T>(nnz); *tmpz = a.take<T>(nnz);
-    *ck_y = a.take<T>((int64_t)nck * nnz);
-    *ck_Q = a.take<T>((int64_t)nck * m * ldq0);
-    *sg_y = a.take<T>((int64_t)ckpt * nnz);
-    *sg_yc = a.take<T>((int64_t)ckpt * nnz);
-    *sg_d = a.take<T>((int64_t)ckpt * nnz);
-    *sg_U = a.take<T>((int64_t)ckpt * m * ldq0);
-    *sg_V = a.take<T>((int64_t)ckpt * n * ldq0);
-    *fin_V = a.take<T>(n * ldq0);
-    *vals_in = a.take<T>(nnz); *hvals_in = a.take<T>(nh);
-    *part3 = a.take<double>(8);
-    W.layout(a);
-    A.layout(a);
-  };
+  int nck = 0;
+  int64_t ldq0 = 0;
   T *a_csr, *y_csr, *hv, *xh, *gH, *ybar, *abar, *tmpz, *ck_y, *ck_Q, *sg_y, *sg_yc, *sg_d, *sg_U,
       *sg_V, *fin_V, *vals_in, *hvals_in;
   double* part3;
-  Arena a0;
-  layout_all(a0, &a_csr, &y_csr, &hv, &xh, &gH, &ybar, &abar, &tmpz, &ck_y, &ck_Q, &sg_y, &sg_yc,
-             &sg_d, &sg_U, &sg_V, &fin_V, &vals_in, &hvals_in, &part3);
-  DeviceBlock wb;
-  SVT_TRY(wb.alloc(a0.off, st));
-  Arena a1; a1.base = (char*)wb.ptr;
-  layout_all(a1, &a_csr, &y_csr, &hv, &xh, &gH, &ybar, &abar, &tmpz, &ck_y, &ck_Q, &sg_y, &sg_yc,
-             &sg_d, &sg_U, &sg_V, &fin_V, &vals_in, &hvals_in, &part3);
-  SVT_CUDA(cudaMemsetAsync(W.flags, 0, kFlagWords * sizeof(unsigned), st));
-  SVT_CUDA(cudaMemsetAsync(A.zero_l, 0, A.zmax * sizeof(T), st));
-  DeviceBlock t1, t2;
-  const bool dbl_in = opt->precision == SVT_FP64;
-  SVT_TRY(upload<T>(vals, nnz, vals_in, dbl_in, st, t1));
-  SVT_TRY(upload<T>(hvals, nh, hvals_in, dbl_in, st, t2));
-  SVT_TRY((gather_convert<T, T>(nnz, pl->csr_src, vals_in, a_csr, st)));
-  SVT_TRY((gather_convert<T, T>(nh, ph->csr_src, hvals_in, hv, st)));
-  // initialisation (Algorithm 4): power steps for ||P_Lambda A||_2, k0, Y = k0 delta A
-  SVT_TRY(launch_gather<T>(nnz, pl->perm, a_csr, W.y_csc, st));
-  SVT_TRY(launch_gaussian<double>(P.seed, kPowerSeedIter, 0, n, 1, W.pw, 1, st));
-  SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
-  k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
-  SVT_LAUNCH_CHECK();
-  for (int it = 0; it < P.power_steps; ++it) {
-    SVT_TRY((launch_spmm_rows<T, double>(m, pl->row_ptr, pl->col_idx, a_csr, W.pv, 1, 1, W.pu, 1,
-                                         W.spmm_scr, nnz, st, pl->chunk_row_csr)));
-    SVT_TRY((launch_spmm_rows<T, double>(n, pl->col_ptr, pl->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1,
-                                         W.spmm_scr, nnz, st, pl->chunk_row_csc)));
-    SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
-    k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
-    SVT_LAUNCH_CHECK();
-  }
-  double lam2 = 0.0;
-  SVT_CUDA(cudaMemcpyAsync(&lam2, W.dsc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
-  SVT_CUDA(cudaStreamSynchronize(st));
-  const double s2 = std::sqrt(std::sqrt(lam2));
-  const int k0 = s2 > 0.0 ? (int)std::min(std::ceil(tau / (delta * s2)), 2.0e9) : 1;
-
+  int k0 = 1;
   // one SVT iteration from state (y, Q[:, :s], eps_thr, eps_min, normY2)
   struct State {
     int s = 0;
@@ -669,12 +592,26 @@ svt_status unrolled_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     T* V = nullptr;
     T* d = nullptr;
   };
-  auto iterate = [&](State& S, int i, bool update_y, IterOut* io, const Capture* cap) -> svt_status {
+  std::vector<State> cks;
+  State S;
+  IterOut last;
+  std::vector<T> hx;          // X^(T) on the held-out entries, held CSR order
+  std::vector<int32_t> hsrc;  // caller position of each held CSR slot
+  double t_fwd = 0;
+  bool backward_done = false;
+
+  ~UnrolledTape() {
+    if (st) cudaStreamSynchronize(st);
+    svt_pattern_destroy(pl);
+    svt_pattern_destroy(ph);
+  }
+
+  svt_status iterate(State& Sx, int i, bool update_y, IterOut* io, const Capture* cap) {
     R4Out ro;
     SVT_TRY(launch_gather<T>(nnz, pl->perm, y_csr, W.y_csc, st));
-    SVT_TRY(r4svd_run<T>(W, y_csr, W.y_csc, S.Qcur, S.s, S.normY2, S.eps_thr, (uint32_t)i, S.Qnext, &ro));
+    SVT_TRY(r4svd_run<T>(W, y_csr, W.y_csc, Sx.Qcur, Sx.s, Sx.normY2, Sx.eps_thr, (uint32_t)i, Sx.Qnext, &ro));
     if (UP.ritz_maxit > 0)
-      SVT_TRY(ritz_refine<T>(W, A, pl, y_csr, W.y_csc, S.Qcur, S.Qnext, tau, UP.ritz_tol, UP.ritz_maxit,
+      SVT_TRY(ritz_refine<T>(W, A, pl, y_csr, W.y_csc, Sx.Qcur, Sx.Qnext, tau, UP.ritz_tol, UP.ritz_maxit,
                              (uint32_t)i, &ro, &ritz));
     int k = 0;
     while (k < ro.r && ro.sigma[k] > tau) ++k;
@@ -686,173 +623,244 @@ svt_status unrolled_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     if (cap) {  // V_K = B^T U_B,K Sigma_K^-1 and U_K
       SVT_TRY(scaled_right<T>(W, ro.r, k, inv));
       SVT_TRY((copy_convert<T, T>(n, k, W.Wk, W.ldk, cap->V, ldq0, st)));
-      SVT_TRY((copy_convert<T, T>(m, k, S.Qnext, W.ldq, cap->U, ldq0, st)));
+      SVT_TRY((copy_convert<T, T>(m, k, Sx.Qnext, W.ldq, cap->U, ldq0, st)));
     }
     SVT_TRY(scaled_right<T>(W, ro.r, k, coef));
     if (cap) {  // A - X on Lambda: the sampled update of a zero vector with step 1
       SVT_CUDA(cudaMemsetAsync(cap->d, 0, nnz * sizeof(T), st));
-      SVT_TRY(sampled_update<T>(pl, S.Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, cap->d, 1.0, part3, W.part,
+      SVT_TRY(sampled_update<T>(pl, Sx.Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, cap->d, 1.0, part3, W.part,
                                 W.flags, st, true));
     }
     io->r = ro.r; io->k = k;
     io->sigma.assign(ro.sigma.begin(), ro.sigma.begin() + k);
     if (!update_y) return SVT_OK;
-    SVT_TRY(sampled_update<T>(pl, S.Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
+    SVT_TRY(sampled_update<T>(pl, Sx.Qnext, W.ldq, W.Wk, W.ldk, k, a_csr, y_csr, delta, W.dsc + 5,
                               W.part, W.flags, st, true));
     double sums[3];
     SVT_CUDA(cudaMemcpyAsync(sums, W.dsc + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaStreamSynchronize(st));
     const double res = std::sqrt(sums[0]);  // cooling compares successive residuals only
     if (!std::isfinite(res)) return fail(SVT_ERR_NUMERIC, "unrolled: non-finite iterate at %d", i);
-    if (res < S.eps_min) S.eps_min = res; else S.eps_thr *= P.beta;
-    S.normY2 = sums[2];
-    std::swap(S.Qcur, S.Qnext);
-    S.s = ro.r;
+    if (res < Sx.eps_min) Sx.eps_min = res; else Sx.eps_thr *= P.beta;
+    Sx.normY2 = sums[2];
+    std::swap(Sx.Qcur, Sx.Qnext);
+    Sx.s = ro.r;
     return SVT_OK;
-  };
-  auto norm_y = [&](double* out) -> svt_status {
+  }
+
+  svt_status norm_y(double* out) {
     SVT_TRY(sumsq<T>(nnz, y_csr, W.dsc + 4, W.part, st));
     SVT_CUDA(cudaMemcpyAsync(out, W.dsc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaStreamSynchronize(st));
     return SVT_OK;
-  };
+  }
 
-  // ---------------- forward with checkpoints
-  std::vector<State> cks(nck);
-  State S;
-  S.eps_thr = P.eps_thr0; S.Qcur = W.Qa; S.Qnext = W.Qb;
-  SVT_TRY(scale_copy<T>(nnz, a_csr, (double)k0 * delta, y_csr, st));
-  SVT_TRY(norm_y(&S.normY2));
-  IterOut last;
-  for (int i = 1; i <= steps; ++i) {
-    if ((i - 1) % ckpt == 0) {
-      const int c = (i - 1) / ckpt;
-      cks[c] = S;
-      SVT_CUDA(cudaMemcpyAsync(ck_y + (int64_t)c * nnz, y_csr, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
-      SVT_CUDA(cudaMemcpyAsync(ck_Q + (int64_t)c * m * ldq0, S.Qcur, m * ldq0 * sizeof(T),
-                               cudaMemcpyDeviceToDevice, st));
+  // Forward pass: T iterations from Y^(1) = k0 delta P_Lambda(A), checkpoints every ckpt
+  // iterations, and X^(T) on the held-out entries (hx).
+  svt_status forward(int64_t m_, int64_t n_, int64_t nnz_, const int32_t* rows, const int32_t* cols,
+                     const void* vals, int64_t nh_, const int32_t* hrows, const int32_t* hcols,
+                     double tau_, double delta_, const svt_unrolled_params& up, const svt_options* opt) {
+    t0 = std::chrono::steady_clock::now();
+    m = m_; n = n_; nnz = nnz_; nh = nh_; tau = tau_; delta = delta_; UP = up;
+    SVT_TRY(make_params(m, n, opt, &P));
+    st = (cudaStream_t)opt->stream;
+    dbl_in = opt->precision == SVT_FP64;
+    const int steps = UP.steps, ckpt = UP.checkpoint_every;
+    // index arrays on the device
+    Arena ia;
+    ia.take<int32_t>(nnz); ia.take<int32_t>(nnz); ia.take<int32_t>(nh); ia.take<int32_t>(nh);
+    SVT_TRY(idx_blk.alloc(ia.off, st));
+    Arena ib; ib.base = (char*)idx_blk.ptr;
+    int32_t* d_rows = ib.take<int32_t>(nnz);
+    int32_t* d_cols = ib.take<int32_t>(nnz);
+    int32_t* d_hrows = ib.take<int32_t>(nh);
+    int32_t* d_hcols = ib.take<int32_t>(nh);
+    SVT_TRY(upload_idx<T>(rows, nnz, d_rows, st));
+    SVT_TRY(upload_idx<T>(cols, nnz, d_cols, st));
+    SVT_TRY(upload_idx<T>(hrows, nh, d_hrows, st));
+    SVT_TRY(upload_idx<T>(hcols, nh, d_hcols, st));
+    SVT_TRY(build_pattern(m, n, nnz, d_rows, d_cols, st, &pl));
+    SVT_TRY(build_pattern(m, n, nh, d_hrows, d_hcols, st, &ph));
+    if (nnz == 0 || nh == 0) return fail(SVT_ERR_ARG, "unrolled: need observed and held-out entries");
+
+    W.P = P; W.pat = pl; W.s = st;
+    A.m = m; A.n = n; A.zl = nnz; A.zmax = std::max(nnz, nh); A.kcap = P.r_cap;
+    nck = (steps + ckpt - 1) / ckpt;
+    ldq0 = ld_of(P.r_cap);
+    auto layout_all = [&](Arena& a) {
+      a_csr = a.take<T>(nnz); y_csr = a.take<T>(nnz);
+      hv = a.take<T>(nh); xh = a.take<T>(nh); gH = a.take<T>(nh);
+      ybar = a.take<T>(nnz); abar = a.take<T>(nnz); tmpz = a.take<T>(nnz);
+      ck_y = a.take<T>((int64_t)nck * nnz);
+      ck_Q = a.take<T>((int64_t)nck * m * ldq0);
+      sg_y = a.take<T>((int64_t)ckpt * nnz);
+      sg_yc = a.take<T>((int64_t)ckpt * nnz);
+      sg_d = a.take<T>((int64_t)ckpt * nnz);
+      sg_U = a.take<T>((int64_t)ckpt * m * ldq0);
+      sg_V = a.take<T>((int64_t)ckpt * n * ldq0);
+      fin_V = a.take<T>(n * ldq0);
+      vals_in = a.take<T>(nnz); hvals_in = a.take<T>(nh);
+      part3 = a.take<double>(8);
+      W.layout(a);
+      A.layout(a);
+    };
+    Arena a0;
+    layout_all(a0);
+    SVT_TRY(wb.alloc(a0.off, st));
+    Arena a1; a1.base = (char*)wb.ptr;
+    layout_all(a1);
+    SVT_CUDA(cudaMemsetAsync(W.flags, 0, kFlagWords * sizeof(unsigned), st));
+    SVT_CUDA(cudaMemsetAsync(A.zero_l, 0, A.zmax * sizeof(T), st));
+    SVT_TRY(upload<T>(vals, nnz, vals_in, dbl_in, st, t1));
+    SVT_TRY((gather_convert<T, T>(nnz, pl->csr_src, vals_in, a_csr, st)));
+    // initialisation (Algorithm 4): power steps for ||P_Lambda A||_2, k0, Y = k0 delta A
+    SVT_TRY(launch_gather<T>(nnz, pl->perm, a_csr, W.y_csc, st));
+    SVT_TRY(launch_gaussian<double>(P.seed, kPowerSeedIter, 0, n, 1, W.pw, 1, st));
+    SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
+    k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
+    SVT_LAUNCH_CHECK();
+    for (int it = 0; it < P.power_steps; ++it) {
+      SVT_TRY((launch_spmm_rows<T, double>(m, pl->row_ptr, pl->col_idx, a_csr, W.pv, 1, 1, W.pu, 1,
+                                           W.spmm_scr, nnz, st, pl->chunk_row_csr)));
+      SVT_TRY((launch_spmm_rows<T, double>(n, pl->col_ptr, pl->row_idx, W.y_csc, W.pu, 1, 1, W.pw, 1,
+                                           W.spmm_scr, nnz, st, pl->chunk_row_csc)));
+      SVT_TRY(sumsq<double>(n, W.pw, W.dsc + 3, W.part, st));
+      k_normalize<<<(int)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(n, W.pw, W.dsc + 3, W.pv);
+      SVT_LAUNCH_CHECK();
     }
-    SVT_TRY(iterate(S, i, i < steps, &last, nullptr));
-  }
-  // X^(T) on the held-out set: sampled product with a = 0 and step -1 gives x
-  SVT_CUDA(cudaMemsetAsync(xh, 0, nh * sizeof(T), st));
-  SVT_TRY(sampled_update<T>(ph, S.Qnext, W.ldq, W.Wk, W.ldk, last.k, A.zero_l, xh, -1.0, part3,
-                            W.part, W.flags, st));
-  std::vector<T> hx(nh), hvh(nh);
-  SVT_CUDA(cudaMemcpyAsync(hx.data(), xh, nh * sizeof(T), cudaMemcpyDeviceToHost, st));
-  SVT_CUDA(cudaMemcpyAsync(hvh.data(), hv, nh * sizeof(T), cudaMemcpyDeviceToHost, st));
-  SVT_CUDA(cudaStreamSynchronize(st));
-  double loss = 0.0;
-  std::vector<T> g(nh);
-  for (int64_t e = 0; e < nh; ++e) {
-    const double rres = (double)hx[e] - (double)hvh[e];
-    loss += rres * rres;
-    g[e] = (T)(2.0 * rres / (double)nh);
-  }
-  loss /= (double)nh;
-  const double t_fwd = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (!grad_vals) {  // forward only
-    std::vector<int32_t> hsrc(nh);
+    double lam2 = 0.0;
+    SVT_CUDA(cudaMemcpyAsync(&lam2, W.dsc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaStreamSynchronize(st));
+    const double s2 = std::sqrt(std::sqrt(lam2));
+    k0 = s2 > 0.0 ? (int)std::min(std::ceil(tau / (delta * s2)), 2.0e9) : 1;
+
+    // forward with checkpoints
+    cks.assign(nck, State());
+    S = State();
+    S.eps_thr = P.eps_thr0; S.Qcur = W.Qa; S.Qnext = W.Qb;
+    SVT_TRY(scale_copy<T>(nnz, a_csr, (double)k0 * delta, y_csr, st));
+    SVT_TRY(norm_y(&S.normY2));
+    for (int i = 1; i <= steps; ++i) {
+      if ((i - 1) % ckpt == 0) {
+        const int c = (i - 1) / ckpt;
+        cks[c] = S;
+        SVT_CUDA(cudaMemcpyAsync(ck_y + (int64_t)c * nnz, y_csr, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        SVT_CUDA(cudaMemcpyAsync(ck_Q + (int64_t)c * m * ldq0, S.Qcur, m * ldq0 * sizeof(T),
+                                 cudaMemcpyDeviceToDevice, st));
+      }
+      SVT_TRY(iterate(S, i, i < steps, &last, nullptr));
+    }
+    // X^(T) on the held-out set: sampled product with a = 0 and step -1 gives x
+    SVT_CUDA(cudaMemsetAsync(xh, 0, nh * sizeof(T), st));
+    SVT_TRY(sampled_update<T>(ph, S.Qnext, W.ldq, W.Wk, W.ldk, last.k, A.zero_l, xh, -1.0, part3,
+                              W.part, W.flags, st));
+    hx.resize(nh);
+    hsrc.resize(nh);
+    SVT_CUDA(cudaMemcpyAsync(hx.data(), xh, nh * sizeof(T), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaMemcpyAsync(hsrc.data(), ph->csr_src, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaStreamSynchronize(st));
-    std::vector<double> xhold(nh);
-    for (int64_t e = 0; e < nh; ++e) xhold[hsrc[e]] = (double)hx[e];
-    if (x_held) SVT_CUDA(cudaMemcpyAsync(x_held, xhold.data(), nh * sizeof(double), cudaMemcpyDefault, st));
-    SVT_CUDA(cudaStreamSynchronize(st));
-    if (out3) { out3[0] = loss; out3[1] = NAN; out3[2] = NAN; }
-    if (info) {
-      info->k0 = k0; info->k_final = last.k; info->r_final = last.r;
-      info->ritz_steps = ritz.steps; info->ritz_capped = ritz.capped; info->ritz_grown = ritz.grown;
-      info->loss = loss; info->seconds_forward = t_fwd; info->seconds_total = t_fwd;
-    }
+    t_fwd = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return SVT_OK;
   }
 
-  // ---------------- backward
-  CgStats cg;
-  double gtau = 0.0, gdelta = 0.0, trace = 0.0;
-  SVT_CUDA(cudaMemcpyAsync(gH, g.data(), nh * sizeof(T), cudaMemcpyHostToDevice, st));
-  // triplets of the last iterate: U = Qnext[:, :k], V = B^T U_B,K Sigma_K^-1
-  {
-    std::vector<double> inv(last.k);
-    for (int j = 0; j < last.k; ++j) inv[j] = 1.0 / last.sigma[j];
-    SVT_TRY(scaled_right<T>(W, last.r, last.k, inv));
+  // X^(T) on the held-out entries in the caller's order.
+  void held_predictions(std::vector<double>* out) const {
+    out->assign(nh, 0.0);
+    for (int64_t e = 0; e < nh; ++e) (*out)[hsrc[e]] = (double)hx[e];
   }
-  // (W.Bt / W.Ub still hold the last iteration; scaled_right wrote V_K into W.Wk)
-  SVT_TRY((copy_convert<T, T>(n, last.k, W.Wk, W.ldk, fin_V, ldq0, st)));
-  Triplets<T> XT;
-  XT.U = S.Qnext; XT.ldu = W.ldq; XT.V = fin_V; XT.ldv = ldq0; XT.sigma = last.sigma; XT.k = last.k;
-  XT.y_csr = y_csr;
-  SVT_TRY(launch_gather<T>(nnz, pl->perm, y_csr, tmpz, st));
-  XT.y_csc = tmpz;
-  SVT_CUDA(cudaMemsetAsync(ybar, 0, nnz * sizeof(T), st));
-  SVT_CUDA(cudaMemsetAsync(abar, 0, nnz * sizeof(T), st));
-  SVT_TRY(jvp_sampled<T>(A, pl, ph, gH, XT, tau, ybar, 1.0, &trace, cg_tol, cg_maxit, &cg, part3,
-                         W.flags, st));
-  gtau -= trace;  // <G, dX/dtau> = -trace(U^T G V)
-  // segments in reverse: iterations 1..steps-1 need the backward step
-  for (int c = nck - 1; c >= 0; --c) {
-    const int i0 = c * ckpt + 1;
-    const int i1 = std::min(i0 + ckpt - 1, steps - 1);
-    if (i0 > i1) continue;
-    // replay the segment from its checkpoint, keeping each iterate's Y, triplets and A - X
-    State R = cks[c];
-    SVT_CUDA(cudaMemcpyAsync(y_csr, ck_y + (int64_t)c * nnz, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    SVT_CUDA(cudaMemcpyAsync(R.Qcur, ck_Q + (int64_t)c * m * ldq0, m * ldq0 * sizeof(T),
-                             cudaMemcpyDeviceToDevice, st));
-    std::vector<IterOut> outs(i1 - i0 + 1);
-    for (int i = i0; i <= i1; ++i) {
-      const int j = i - i0;
-      SVT_CUDA(cudaMemcpyAsync(sg_y + (int64_t)j * nnz, y_csr, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
-      SVT_TRY(launch_gather<T>(nnz, pl->perm, y_csr, sg_yc + (int64_t)j * nnz, st));
-      Capture cap;
-      cap.U = sg_U + (int64_t)j * m * ldq0;
-      cap.V = sg_V + (int64_t)j * n * ldq0;
-      cap.d = sg_d + (int64_t)j * nnz;
-      SVT_TRY(iterate(R, i, true, &outs[j], &cap));
+
+  // Reverse pass for g = dL/dX^(T) on the held-out entries (caller order): grad (caller
+  // order, nnz) = dL/dvals, *gtau, *gdelta.
+  svt_status backward(const std::vector<double>& g_caller, std::vector<double>* grad, double* gtau_out,
+                      double* gdelta_out) {
+    const int steps = UP.steps, ckpt = UP.checkpoint_every;
+    const double cg_tol = UP.cg_tol;
+    const int cg_maxit = UP.cg_maxit;
+    std::vector<T> g(nh);
+    for (int64_t e = 0; e < nh; ++e) g[e] = (T)g_caller[hsrc[e]];
+    double gtau = 0.0, gdelta = 0.0, trace = 0.0;
+    SVT_CUDA(cudaMemcpyAsync(gH, g.data(), nh * sizeof(T), cudaMemcpyHostToDevice, st));
+    // triplets of the last iterate: U = Qnext[:, :k], V = B^T U_B,K Sigma_K^-1
+    {
+      std::vector<double> inv(last.k);
+      for (int j = 0; j < last.k; ++j) inv[j] = 1.0 / last.sigma[j];
+      SVT_TRY(scaled_right<T>(W, last.r, last.k, inv));
     }
-    for (int i = i1; i >= i0; --i) {
-      const int j = i - i0;
-      const T* d_i = sg_d + (int64_t)j * nnz;
-      // Y^(i+1) = Y^(i) + delta P(A - X^(i)):  abar += delta ybar, dbar += <ybar, A - X^(i)>
-      k_vec_axpy<T><<<egrid(nnz), 256, 0, st>>>(nnz, delta, ybar, abar);
-      SVT_LAUNCH_CHECK();
-      double dd = 0.0;
-      SVT_TRY(dot<T>(A, nnz, ybar, d_i, &dd, st));
-      gdelta += dd;
-      Triplets<T> Xi;
-      Xi.U = sg_U + (int64_t)j * m * ldq0; Xi.ldu = ldq0;
-      Xi.V = sg_V + (int64_t)j * n * ldq0; Xi.ldv = ldq0;
-      Xi.sigma = outs[j].sigma; Xi.k = outs[j].k;
-      Xi.y_csr = sg_y + (int64_t)j * nnz; Xi.y_csc = sg_yc + (int64_t)j * nnz;
-      // ybar <- ybar - delta J_i(ybar);  tau: -delta <ybar, dX/dtau> = +delta trace
-      SVT_TRY(jvp_sampled<T>(A, pl, pl, ybar, Xi, tau, ybar, -delta, &trace, cg_tol, cg_maxit, &cg,
-                             part3, W.flags, st));
-      gtau += delta * trace;
+    // (W.Bt / W.Ub still hold the last iteration; scaled_right wrote V_K into W.Wk)
+    SVT_TRY((copy_convert<T, T>(n, last.k, W.Wk, W.ldk, fin_V, ldq0, st)));
+    Triplets<T> XT;
+    XT.U = S.Qnext; XT.ldu = W.ldq; XT.V = fin_V; XT.ldv = ldq0; XT.sigma = last.sigma; XT.k = last.k;
+    XT.y_csr = y_csr;
+    SVT_TRY(launch_gather<T>(nnz, pl->perm, y_csr, tmpz, st));
+    XT.y_csc = tmpz;
+    SVT_CUDA(cudaMemsetAsync(ybar, 0, nnz * sizeof(T), st));
+    SVT_CUDA(cudaMemsetAsync(abar, 0, nnz * sizeof(T), st));
+    SVT_TRY(jvp_sampled<T>(A, pl, ph, gH, XT, tau, ybar, 1.0, &trace, cg_tol, cg_maxit, &cg, part3,
+                           W.flags, st));
+    gtau -= trace;  // <G, dX/dtau> = -trace(U^T G V)
+    // segments in reverse: iterations 1..steps-1 need the backward step
+    for (int c = nck - 1; c >= 0; --c) {
+      const int i0 = c * ckpt + 1;
+      const int i1 = std::min(i0 + ckpt - 1, steps - 1);
+      if (i0 > i1) continue;
+      // replay the segment from its checkpoint, keeping each iterate's Y, triplets and A - X
+      State R = cks[c];
+      SVT_CUDA(cudaMemcpyAsync(y_csr, ck_y + (int64_t)c * nnz, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      SVT_CUDA(cudaMemcpyAsync(R.Qcur, ck_Q + (int64_t)c * m * ldq0, m * ldq0 * sizeof(T),
+                               cudaMemcpyDeviceToDevice, st));
+      std::vector<IterOut> outs(i1 - i0 + 1);
+      for (int i = i0; i <= i1; ++i) {
+        const int j = i - i0;
+        SVT_CUDA(cudaMemcpyAsync(sg_y + (int64_t)j * nnz, y_csr, nnz * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        SVT_TRY(launch_gather<T>(nnz, pl->perm, y_csr, sg_yc + (int64_t)j * nnz, st));
+        Capture cap;
+        cap.U = sg_U + (int64_t)j * m * ldq0;
+        cap.V = sg_V + (int64_t)j * n * ldq0;
+        cap.d = sg_d + (int64_t)j * nnz;
+        SVT_TRY(iterate(R, i, true, &outs[j], &cap));
+      }
+      for (int i = i1; i >= i0; --i) {
+        const int j = i - i0;
+        const T* d_i = sg_d + (int64_t)j * nnz;
+        // Y^(i+1) = Y^(i) + delta P(A - X^(i)):  abar += delta ybar, dbar += <ybar, A - X^(i)>
+        k_vec_axpy<T><<<egrid(nnz), 256, 0, st>>>(nnz, delta, ybar, abar);
+        SVT_LAUNCH_CHECK();
+        double dd = 0.0;
+        SVT_TRY(dot<T>(A, nnz, ybar, d_i, &dd, st));
+        gdelta += dd;
+        Triplets<T> Xi;
+        Xi.U = sg_U + (int64_t)j * m * ldq0; Xi.ldu = ldq0;
+        Xi.V = sg_V + (int64_t)j * n * ldq0; Xi.ldv = ldq0;
+        Xi.sigma = outs[j].sigma; Xi.k = outs[j].k;
+        Xi.y_csr = sg_y + (int64_t)j * nnz; Xi.y_csc = sg_yc + (int64_t)j * nnz;
+        // ybar <- ybar - delta J_i(ybar);  tau: -delta <ybar, dX/dtau> = +delta trace
+        SVT_TRY(jvp_sampled<T>(A, pl, pl, ybar, Xi, tau, ybar, -delta, &trace, cg_tol, cg_maxit, &cg,
+                               part3, W.flags, st));
+        gtau += delta * trace;
+      }
     }
+    // Y^(1) = k0 delta A
+    k_vec_axpy<T><<<egrid(nnz), 256, 0, st>>>(nnz, (double)k0 * delta, ybar, abar);
+    SVT_LAUNCH_CHECK();
+    double ya = 0.0;
+    SVT_TRY(dot<T>(A, nnz, ybar, a_csr, &ya, st));
+    gdelta += (double)k0 * ya;
+    // gradient in the caller's entry order
+    std::vector<T> ab(nnz);
+    std::vector<int32_t> src(nnz);
+    SVT_CUDA(cudaMemcpyAsync(ab.data(), abar, nnz * sizeof(T), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaMemcpyAsync(src.data(), pl->csr_src, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SVT_CUDA(cudaStreamSynchronize(st));
+    grad->assign(nnz, 0.0);
+    for (int64_t e = 0; e < nnz; ++e) (*grad)[src[e]] = (double)ab[e];
+    *gtau_out = gtau;
+    *gdelta_out = gdelta;
+    backward_done = true;
+    return SVT_OK;
   }
-  // Y^(1) = k0 delta A
-  k_vec_axpy<T><<<egrid(nnz), 256, 0, st>>>(nnz, (double)k0 * delta, ybar, abar);
-  SVT_LAUNCH_CHECK();
-  double ya = 0.0;
-  SVT_TRY(dot<T>(A, nnz, ybar, a_csr, &ya, st));
-  gdelta += (double)k0 * ya;
-  // gradient in the caller's entry order
-  std::vector<T> ab(nnz);
-  std::vector<int32_t> src(nnz);
-  SVT_CUDA(cudaMemcpyAsync(ab.data(), abar, nnz * sizeof(T), cudaMemcpyDeviceToHost, st));
-  SVT_CUDA(cudaMemcpyAsync(src.data(), pl->csr_src, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  std::vector<int32_t> hsrc(nh);
-  SVT_CUDA(cudaMemcpyAsync(hsrc.data(), ph->csr_src, nh * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SVT_CUDA(cudaStreamSynchronize(st));
-  std::vector<double> gv(nnz), xhold(nh);
-  for (int64_t e = 0; e < nnz; ++e) gv[src[e]] = (double)ab[e];
-  for (int64_t e = 0; e < nh; ++e) xhold[hsrc[e]] = (double)hx[e];
-  if (grad_vals) SVT_CUDA(cudaMemcpyAsync(grad_vals, gv.data(), nnz * sizeof(double), cudaMemcpyDefault, st));
-  if (x_held) SVT_CUDA(cudaMemcpyAsync(x_held, xhold.data(), nh * sizeof(double), cudaMemcpyDefault, st));
-  SVT_CUDA(cudaStreamSynchronize(st));
-  if (out3) { out3[0] = loss; out3[1] = gtau; out3[2] = gdelta; }
-  if (info) {
+
+  void fill_info(svt_unrolled_info* info, double loss) const {
+    if (!info) return;
     info->k0 = k0;
     info->k_final = last.k;
     info->r_final = last.r;
@@ -865,11 +873,49 @@ svt_status unrolled_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     info->seconds_forward = t_fwd;
     info->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
+};
+
+svt_status check_unrolled_args(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                               const void* vals, int64_t nheld, const int32_t* held_rows,
+                               const int32_t* held_cols, double tau, double delta,
+                               const svt_unrolled_params& up) {
+  if (m <= 0 || n <= 0 || nnz <= 0 || nheld <= 0 || !rows || !cols || !vals || !held_rows ||
+      !held_cols || !(tau > 0.0) || !(delta > 0.0))
+    return fail(SVT_ERR_ARG, "unrolled: bad arguments");
+  if (up.steps < 1 || up.checkpoint_every < 1 || up.cg_maxit < 1 || up.ritz_maxit < 0 ||
+      !(up.cg_tol > 0.0) || !(up.ritz_tol > 0.0))
+    return fail(SVT_ERR_ARG, "unrolled: bad parameters (steps, checkpoint_every, cg_maxit >= 1; "
+                             "ritz_maxit >= 0; cg_tol, ritz_tol > 0)");
+  return SVT_OK;
+}
+
+// Copy n doubles (host or device) into a host vector.
+svt_status fetch_doubles(const double* src, int64_t count, std::vector<double>* out) {
+  out->resize(count);
+  if (count <= 0) return SVT_OK;
+  SVT_CUDA(cudaMemcpy(out->data(), src, count * sizeof(double), cudaMemcpyDefault));
+  return SVT_OK;
+}
+
+svt_status store_doubles(const std::vector<double>& v, double* dst) {
+  if (!dst || v.empty()) return SVT_OK;
+  SVT_CUDA(cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyDefault));
   return SVT_OK;
 }
 
 }  // namespace
 }  // namespace svt
+
+// The opaque tape of the ABI: one precision's tape.
+struct svt_unrolled_tape {
+  int precision = SVT_FP64;
+  svt::UnrolledTape<double>* d = nullptr;
+  svt::UnrolledTape<float>* f = nullptr;
+  ~svt_unrolled_tape() {
+    delete d;
+    delete f;
+  }
+};
 
 extern "C" void svt_unrolled_default_params(svt_unrolled_params* p, int precision) {
   if (!p) return;
@@ -881,6 +927,70 @@ extern "C" void svt_unrolled_default_params(svt_unrolled_params* p, int precisio
   p->ritz_tol = precision == SVT_MIXED_FP32 ? 2e-6 : 1e-11;
 }
 
+extern "C" svt_status svt_unrolled_forward(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
+                                           const int32_t* cols, const void* vals, int64_t nheld,
+                                           const int32_t* held_rows, const int32_t* held_cols,
+                                           double tau, double delta, const svt_unrolled_params* p,
+                                           const svt_options* opt, double* x_held,
+                                           svt_unrolled_info* info, svt_unrolled_tape** tape) {
+  using namespace svt;
+  if (info) memset(info, 0, sizeof(*info));
+  if (tape) *tape = nullptr;
+  if (!opt) return fail(SVT_ERR_ARG, "unrolled: null options");
+  if (opt->precision != SVT_FP64 && opt->precision != SVT_MIXED_FP32)
+    return fail(SVT_ERR_ARG, "unrolled: unknown precision");
+  svt_unrolled_params up;
+  if (p) up = *p;
+  else svt_unrolled_default_params(&up, opt->precision);
+  SVT_TRY(check_unrolled_args(m, n, nnz, rows, cols, vals, nheld, held_rows, held_cols, tau, delta, up));
+  svt_unrolled_tape* t = new svt_unrolled_tape;
+  t->precision = opt->precision;
+  svt_status st;
+  std::vector<double> xh;
+  if (opt->precision == SVT_FP64) {
+    t->d = new UnrolledTape<double>;
+    st = t->d->forward(m, n, nnz, rows, cols, vals, nheld, held_rows, held_cols, tau, delta, up, opt);
+    if (st >= 0) { t->d->held_predictions(&xh); t->d->fill_info(info, NAN); }
+  } else {
+    t->f = new UnrolledTape<float>;
+    st = t->f->forward(m, n, nnz, rows, cols, vals, nheld, held_rows, held_cols, tau, delta, up, opt);
+    if (st >= 0) { t->f->held_predictions(&xh); t->f->fill_info(info, NAN); }
+  }
+  if (st >= 0) st = store_doubles(xh, x_held);
+  if (st < 0 || !tape) {
+    delete t;  // synchronises the stream and releases the device memory
+    return st;
+  }
+  *tape = t;
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_unrolled_backward(svt_unrolled_tape* tape, const double* g_held,
+                                            double* grad_vals, double* grad_tau_delta,
+                                            svt_unrolled_info* info) {
+  using namespace svt;
+  if (!tape || !g_held) return fail(SVT_ERR_ARG, "unrolled_backward: null tape or gradient");
+  auto run = [&](auto* T_) -> svt_status {
+    if (T_->backward_done) return fail(SVT_ERR_ARG, "unrolled_backward: the tape was already used");
+    std::vector<double> g, grad;
+    SVT_TRY(fetch_doubles(g_held, T_->nh, &g));
+    double gt = 0.0, gd = 0.0;
+    SVT_TRY(T_->backward(g, &grad, &gt, &gd));
+    SVT_TRY(store_doubles(grad, grad_vals));
+    if (grad_tau_delta) {
+      const double two[2] = {gt, gd};
+      SVT_CUDA(cudaMemcpy(grad_tau_delta, two, sizeof(two), cudaMemcpyDefault));
+    }
+    if (info) { memset(info, 0, sizeof(*info)); T_->fill_info(info, NAN); }
+    return SVT_OK;
+  };
+  const svt_status st = tape->d ? run(tape->d) : run(tape->f);
+  if (st < 0) cudaStreamSynchronize(tape->d ? tape->d->st : tape->f->st);
+  return st;
+}
+
+extern "C" void svt_unrolled_tape_destroy(svt_unrolled_tape* tape) { delete tape; }
+
 extern "C" svt_status svt_unrolled_grad(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                                         const int32_t* cols, const void* vals, int64_t nheld,
                                         const int32_t* held_rows, const int32_t* held_cols,
@@ -891,25 +1001,38 @@ extern "C" svt_status svt_unrolled_grad(int64_t m, int64_t n, int64_t nnz, const
   using namespace svt;
   if (info) memset(info, 0, sizeof(*info));
   if (!opt) return fail(SVT_ERR_ARG, "unrolled_grad: null options");
-  svt_unrolled_params up;
-  if (p) up = *p;
-  else svt_unrolled_default_params(&up, opt->precision);
-  if (m <= 0 || n <= 0 || nnz <= 0 || nheld <= 0 || !rows || !cols || !vals || !held_rows ||
-      !held_cols || !held_vals || !(tau > 0.0) || !(delta > 0.0))
-    return fail(SVT_ERR_ARG, "unrolled_grad: bad arguments");
-  if (up.steps < 1 || up.checkpoint_every < 1 || up.cg_maxit < 1 || up.ritz_maxit < 0 ||
-      !(up.cg_tol > 0.0) || !(up.ritz_tol > 0.0))
-    return fail(SVT_ERR_ARG, "unrolled_grad: bad parameters (steps, checkpoint_every, cg_maxit >= 1; "
-                             "ritz_maxit >= 0; cg_tol, ritz_tol > 0)");
-  svt_status st;
-  if (opt->precision == SVT_FP64)
-    st = unrolled_impl<double>(m, n, nnz, rows, cols, vals, nheld, held_rows, held_cols, held_vals, tau,
-                               delta, up, opt, grad_vals, x_held, out3, info);
-  else if (opt->precision == SVT_MIXED_FP32)
-    st = unrolled_impl<float>(m, n, nnz, rows, cols, vals, nheld, held_rows, held_cols, held_vals, tau,
-                              delta, up, opt, grad_vals, x_held, out3, info);
-  else
-    st = fail(SVT_ERR_ARG, "unrolled_grad: unknown precision");
-  if (st < 0) cudaStreamSynchronize((cudaStream_t)opt->stream);
-  return st;
+  if (!held_vals) return fail(SVT_ERR_ARG, "unrolled_grad: bad arguments");
+  // held-out values in binary64, caller order (host or device input)
+  std::vector<double> hv(nheld > 0 ? nheld : 0);
+  svt_unrolled_tape* tape = nullptr;
+  std::vector<double> xh(nheld > 0 ? nheld : 0);
+  svt_status st = svt_unrolled_forward(m, n, nnz, rows, cols, vals, nheld, held_rows, held_cols, tau,
+                                       delta, p, opt, xh.data(), info, grad_vals ? &tape : nullptr);
+  if (st < 0) return st;
+  struct Guard { svt_unrolled_tape* t; ~Guard() { delete t; } } guard{tape};
+  if (opt->precision == SVT_FP64) {
+    SVT_CUDA(cudaMemcpy(hv.data(), held_vals, nheld * sizeof(double), cudaMemcpyDefault));
+  } else {
+    std::vector<float> h32(nheld);
+    SVT_CUDA(cudaMemcpy(h32.data(), held_vals, nheld * sizeof(float), cudaMemcpyDefault));
+    for (int64_t e = 0; e < nheld; ++e) hv[e] = (double)h32[e];
+  }
+  // L = mean over the held-out entries of (X^(T) - A)^2, dL/dX = 2 (X - A) / nheld
+  double loss = 0.0;
+  std::vector<double> g(nheld);
+  for (int64_t e = 0; e < nheld; ++e) {
+    const double r = xh[e] - hv[e];
+    loss += r * r;
+    g[e] = 2.0 * r / (double)nheld;
+  }
+  loss /= (double)nheld;
+  if (x_held) SVT_TRY(store_doubles(xh, x_held));
+  double gtd[2] = {NAN, NAN};
+  if (tape) {
+    st = svt_unrolled_backward(tape, g.data(), grad_vals, gtd, info);
+    if (st < 0) return st;
+  }
+  if (info) info->loss = loss;
+  if (out3) { out3[0] = loss; out3[1] = gtd[0]; out3[2] = gtd[1]; }
+  return SVT_OK;
 }

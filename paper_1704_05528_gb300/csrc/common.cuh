@@ -77,6 +77,40 @@ __device__ __forceinline__ double block_sum(double v, double* smem32) {
   return t;  // valid in thread 0 (and the whole of warp 0)
 }
 
+// Running sums of the sampled updates.  Binary64 data sum in binary64; binary32 data sum in
+// an unevaluated pair hi + lo of binary32 values.
+template <typename T>
+struct SumAcc;
+
+template <>
+struct SumAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_sq(double x) { s = fma(x, x, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// hi + lo holds the sum.  Knuth's TwoSum gives the exact error of hi + p, and fma gives
+// the exact error of a rounded product; the intrinsics keep the compiler from fusing
+// the steps that must round separately.
+template <>
+struct SumAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add2(float p, float e) {
+    const float t = __fadd_rn(hi, p);
+    const float z = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+    hi = t;
+  }
+  __device__ __forceinline__ void add(float x) { add2(x, 0.f); }
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = __fmul_rn(x, x);
+    add2(p, fmaf(x, x, -p));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // ---------------------------------------------------------------- device flags
 // Bits raised by kernels into a device status word and read back by the host.
 // Words of the device status array of a solve.
@@ -106,12 +140,43 @@ struct Arena {
   }
 };
 
-// RAII owner of a stream-ordered allocation.
+// A caller-owned device workspace, used as a stack by the call that received it: while a
+// WorkspaceScope is alive on a thread, every DeviceBlock allocated on that thread is carved
+// from the top of the workspace and released in reverse order.
+struct Workspace {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t top = 0;
+};
+Workspace* current_workspace();
+struct WorkspaceScope {
+  Workspace ws;
+  Workspace* prev;
+  WorkspaceScope(void* base, size_t bytes);
+  ~WorkspaceScope();
+  WorkspaceScope(const WorkspaceScope&) = delete;
+  WorkspaceScope& operator=(const WorkspaceScope&) = delete;
+};
+
+// RAII owner of device scratch: a stream-ordered allocation, or a slice of the thread's
+// current workspace.
 struct DeviceBlock {
   void* ptr = nullptr;
   cudaStream_t stream = nullptr;
-  ~DeviceBlock() {
-    if (ptr) cudaFreeAsync(ptr, stream);
+  Workspace* ws = nullptr;    // non-null: a slice of this workspace
+  size_t ws_prev_top = 0, ws_end = 0;
+  DeviceBlock() = default;
+  DeviceBlock(const DeviceBlock&) = delete;
+  DeviceBlock& operator=(const DeviceBlock&) = delete;
+  ~DeviceBlock() { release(); }
+  void release() {
+    if (ws) {
+      if (ws->top == ws_end) ws->top = ws_prev_top;  // blocks are released in reverse order
+      ws = nullptr;
+    } else if (ptr) {
+      cudaFreeAsync(ptr, stream);
+    }
+    ptr = nullptr;
   }
   svt_status alloc(size_t bytes, cudaStream_t s);
 };
@@ -136,4 +201,5 @@ struct svt_pattern {
   int32_t* chunk_row_csr = nullptr;  // first CSR row touched by each chunk
   int32_t* chunk_row_csc = nullptr;  // first CSC column touched by each chunk
   void* block = nullptr;        // single device allocation holding the arrays
+  svt::DeviceBlock ws_block;    // or: the arrays' slice of a caller workspace
 };

@@ -523,9 +523,14 @@ size_t eig_scratch(int r) {
 }
 
 namespace {
+// Polls of a grid-barrier wait before it gives up (each poll sleeps about 32 ns): 2^24 in
+// normal use; svt_test_set_grid_wait_limit lowers it so that a test can make a wait run out.
+std::atomic<unsigned> g_grid_wait_polls{1u << 24};
+
 // Grid-wide barrier of a cooperative launch: an arrival count and a generation word in
-// global memory (zero before the launch).  Bounded: a wait that runs out returns false.
-__device__ bool grid_barrier(unsigned* bar, unsigned* gen_local) {
+// global memory (zero before the launch).  Bounded: a wait that runs out after `limit`
+// polls returns false.
+__device__ bool grid_barrier(unsigned* bar, unsigned* gen_local, unsigned limit) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -540,7 +545,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned* gen_local) {
       const volatile unsigned* g = &bar[1];
       unsigned spins = 0;
       while (*g == gen) {
-        if (++spins > (1u << 24)) { ok_s = 0; break; }
+        if (++spins > limit) { ok_s = 0; break; }
         __nanosleep(32);
       }
     }
@@ -564,7 +569,8 @@ __device__ bool grid_barrier(unsigned* bar, unsigned* gen_local) {
 // raises FLAG_GRID_TIMEOUT in *status and every CTA stops.
 __global__ void __launch_bounds__(kJacGridThreads)
 k_jacobi32_grid(int r, const double* __restrict__ G, int64_t ldg, float* A, float* A2, float* V,
-                int max_sweeps, int* sweeps_out, unsigned* bar, unsigned* status) {
+                int max_sweeps, int* sweeps_out, unsigned* bar, unsigned* status,
+                unsigned wait_limit) {
   __shared__ float cs_c[512], cs_s[512];
   __shared__ int pp[512], qq[512];
   __shared__ float scale;
@@ -577,7 +583,7 @@ k_jacobi32_grid(int r, const double* __restrict__ G, int64_t ldg, float* A, floa
     __stcg(&A[t], (float)G[(int64_t)a * ldg + b]);
     __stcg(&V[t], a == b ? 1.0f : 0.0f);
   }
-  bool alive = grid_barrier(bar, &gen);
+  bool alive = grid_barrier(bar, &gen, wait_limit);
   if (tid < 32) {
     float mx = 0.f;
     for (int i = tid; i < r; i += 32) mx = fmaxf(mx, fabsf(__ldcg(&A[(int64_t)i * r + i])));
@@ -656,7 +662,7 @@ k_jacobi32_grid(int r, const double* __restrict__ G, int64_t ldg, float* A, floa
           }
         }
       }
-      alive = grid_barrier(bar, &gen);
+      alive = grid_barrier(bar, &gen, wait_limit);
       float* const t = src; src = dst; dst = t;
     }
     if (!rotated || !alive) break;
@@ -726,7 +732,8 @@ svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStre
     float* V_ = w.V32;
     int* so = sweeps_out;
     unsigned* st_ = status ? status : bar + 2;
-    void* args[] = {&rr_, &G_, &ldg_, &A_, &A2_, &V_, &sweeps, &so, &bar, &st_};
+    unsigned limit = g_grid_wait_polls.load(std::memory_order_relaxed);
+    void* args[] = {&rr_, &G_, &ldg_, &A_, &A2_, &V_, &sweeps, &so, &bar, &st_, &limit};
     SVT_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi32_grid, dim3(blocks),
                                          dim3(kJacGridThreads), args, 0, s));
     count_launch();
@@ -830,3 +837,7 @@ svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub,
 }
 
 }  // namespace svt
+
+extern "C" unsigned svt_test_set_grid_wait_limit(unsigned polls) {
+  return svt::g_grid_wait_polls.exchange(polls == 0 ? 1u : polls);
+}

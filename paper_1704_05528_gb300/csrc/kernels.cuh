@@ -12,6 +12,12 @@ namespace svt {
 // pattern.cu ------------------------------------------------------------------
 svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                          const int32_t* cols, cudaStream_t s, svt_pattern** out);
+// Device bytes of a pattern's arrays, and of the scratch its build sorts in.
+size_t pattern_block_bytes(int64_t m, int64_t n, int64_t nnz);
+size_t pattern_scratch_bytes(int64_t nnz);
+// out[c] = first compressed row touched by chunk c of C entries (ptr: nrows + 1 offsets)
+svt_status launch_chunk_rows(int64_t nrows, int64_t C, int64_t nchunks, const int32_t* ptr,
+                             int32_t* out, cudaStream_t s);
 
 // rng.cu ----------------------------------------------------------------------
 template <typename T>

@@ -27,81 +27,16 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc_common.cuh"
 
 namespace svt {
 namespace {
+using namespace tc;
 
 constexpr int kBM = 128;        // rows per tile: one tensor-memory lane per row
 constexpr int kKC = 32;         // K columns per chunk: 128 bytes of binary32
 constexpr int kMaxChunks = 4;   // K <= 128
 constexpr int kThreads = 256;
-constexpr uint32_t kSpinLimit = 1u << 20;
-
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
-               : "memory");
-}
-// Bounded wait for the phase of the given parity; false when it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  for (uint32_t spin = 0; spin < kSpinLimit; ++spin) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          saddr(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
-      : "memory");
-}
-// Shared-memory matrix descriptor of a K-major operand with 128-byte swizzle: rows of 128
-// bytes, groups of eight rows 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
-  uint64_t d = (saddr(p) & 0x3FFFFu) >> 4;  // start address
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused by this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset
-  d |= (uint64_t)1 << 46;                   // descriptor version
-  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-  return d;
-}
-// Instruction descriptor: D binary32, A and B TF32, both K-major, M x N.
-constexpr uint32_t instr_desc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{ .reg .pred p; setp.ne.u32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   saddr(bar))
-               : "memory");
-}
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  return __uint_as_float(h);
-}
-
 // Stages of the A ring: as many 32 KB stages (high and low part of a 128 x 32 chunk) as
 // fit next to U_B^T.
 template <int NPAD>
@@ -322,6 +257,31 @@ __global__ void k_split_bt(int K, int N, int npad, const double* __restrict__ B,
   blo[t] = l;
 }
 
+template <int NPAD>
+cudaError_t set_smem_limit() {
+  return cudaFuncSetAttribute(k_lift_tf32x3<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Layout<NPAD>::bytes);
+}
+
+// shared-memory limits of every instantiation, once per device
+std::mutex g_prep_mu;
+uint64_t g_prep_devices = 0;
+
+template <int NPAD>
+svt_status launch_lift(int64_t M, int K, int N, const CUtensorMap& mA, const CUtensorMap& mBh,
+                       const CUtensorMap& mBl, float* C, int64_t ldc, unsigned* status,
+                       cudaStream_t s) {
+  using L = Layout<NPAD>;
+  const int64_t ntiles = ceil_div(M, (int64_t)kBM);
+  const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
+  k_lift_tf32x3<NPAD><<<grid, kThreads, L::bytes, s>>>((int)M, N, K, mA, mBh, mBl, C, ldc, status);
+  SVT_LAUNCH_CHECK();
+  return SVT_OK;
+}
+
+}  // namespace
+
+namespace tc {
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -350,29 +310,7 @@ bool encode_2d(CUtensorMap* map, const float* base, uint64_t inner, uint64_t out
              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NPAD>
-cudaError_t set_smem_limit() {
-  return cudaFuncSetAttribute(k_lift_tf32x3<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Layout<NPAD>::bytes);
-}
-
-// shared-memory limits of every instantiation, once per device
-std::mutex g_prep_mu;
-uint64_t g_prep_devices = 0;
-
-template <int NPAD>
-svt_status launch_lift(int64_t M, int K, int N, const CUtensorMap& mA, const CUtensorMap& mBh,
-                       const CUtensorMap& mBl, float* C, int64_t ldc, unsigned* status,
-                       cudaStream_t s) {
-  using L = Layout<NPAD>;
-  const int64_t ntiles = ceil_div(M, (int64_t)kBM);
-  const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
-  k_lift_tf32x3<NPAD><<<grid, kThreads, L::bytes, s>>>((int)M, N, K, mA, mBh, mBl, C, ldc, status);
-  SVT_LAUNCH_CHECK();
-  return SVT_OK;
-}
-
-}  // namespace
+}  // namespace tc
 
 // N rounded up to a tile width with an instantiated kernel (shared memory holds U_B^T
 // for up to 160 columns next to the two-stage ring)
@@ -386,7 +324,7 @@ svt_status lift_tc_prepare() {
   std::lock_guard<std::mutex> lk(g_prep_mu);
   const uint64_t bit = 1ull << (dev & 63);
   if (g_prep_devices & bit) return SVT_OK;
-  if (!encode_fn()) return fail(SVT_ERR_UNSUPPORTED, "tensor-core lift: no tensor map encoder");
+  if (!tc::encode_fn()) return fail(SVT_ERR_UNSUPPORTED, "tensor-core lift: no tensor map encoder");
   SVT_CUDA(set_smem_limit<16>()); SVT_CUDA(set_smem_limit<32>()); SVT_CUDA(set_smem_limit<48>());
   SVT_CUDA(set_smem_limit<64>()); SVT_CUDA(set_smem_limit<80>()); SVT_CUDA(set_smem_limit<96>());
   SVT_CUDA(set_smem_limit<112>()); SVT_CUDA(set_smem_limit<128>()); SVT_CUDA(set_smem_limit<144>());
@@ -399,7 +337,7 @@ bool lift_tc_fits(int64_t M, int K, int N, const float* A, int64_t lda, const fl
   return M > 0 && M < (int64_t)INT32_MAX - kBM && K >= 1 && K <= kMaxChunks * kKC && N >= 1 &&
          N <= 160 && lda % 4 == 0 && ldc % 4 == 0 && lda >= K && ldc >= N &&
          reinterpret_cast<uintptr_t>(A) % 16 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0 &&
-         encode_fn() != nullptr;
+         tc::encode_fn() != nullptr;
 }
 
 svt_status lift_tc(int64_t M, int K, int N, const float* A, int64_t lda, const double* B,
@@ -414,9 +352,9 @@ svt_status lift_tc(int64_t M, int K, int N, const float* A, int64_t lda, const d
   k_split_bt<<<(int)ceil_div((int64_t)npad * 128, 256), 256, 0, s>>>(K, N, npad, B, ldb, bhi, blo);
   SVT_LAUNCH_CHECK();
   CUtensorMap mA, mBh, mBl;
-  if (!encode_2d(&mA, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda * 4, kKC, kBM) ||
-      !encode_2d(&mBh, bhi, 128, (uint64_t)npad, 128 * 4, kKC, (uint32_t)npad) ||
-      !encode_2d(&mBl, blo, 128, (uint64_t)npad, 128 * 4, kKC, (uint32_t)npad))
+  if (!tc::encode_2d(&mA, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda * 4, kKC, kBM) ||
+      !tc::encode_2d(&mBh, bhi, 128, (uint64_t)npad, 128 * 4, kKC, (uint32_t)npad) ||
+      !tc::encode_2d(&mBl, blo, 128, (uint64_t)npad, 128 * 4, kKC, (uint32_t)npad))
     return fail(SVT_ERR_CUDA, "tensor-core lift: tensor map encoding failed");
 #define SVT_LIFT(NP) \
   case NP: return launch_lift<NP>(M, K, N, mA, mBh, mBl, C, ldc, status, s)

@@ -224,6 +224,32 @@ int bits_for(uint64_t range) {  // bits needed to represent values in [0, range)
 
 }  // namespace
 
+// The persistent arrays of a pattern, in one block.
+void pattern_layout(Arena& ar, int64_t m, int64_t n, int64_t nnz, svt_pattern* p) {
+  p->row_ptr = ar.take<int32_t>(m + 1);
+  p->col_idx = ar.take<int32_t>(nnz);
+  p->csr_src = ar.take<int32_t>(nnz);
+  p->col_ptr = ar.take<int32_t>(n + 1);
+  p->row_idx = ar.take<int32_t>(nnz);
+  p->perm = ar.take<int32_t>(nnz);
+  p->csr_row = ar.take<int32_t>(nnz);
+  p->chunk = chunk_size(nnz > 0 ? nnz : 1);
+  p->nchunks = ceil_div(nnz, p->chunk);
+  p->chunk_row_csr = ar.take<int32_t>(p->nchunks);
+  p->chunk_row_csc = ar.take<int32_t>(p->nchunks);
+}
+
+// Sort scratch of the build: two key/value buffer pairs, a histogram, a flags word.
+void scratch_layout(Arena& sa, int64_t nnz, uint64_t** k0, uint64_t** k1, int32_t** v0, int32_t** v1,
+                    int32_t** hist, unsigned** flags) {
+  *k0 = sa.take<uint64_t>(nnz);
+  *k1 = sa.take<uint64_t>(nnz);
+  *v0 = sa.take<int32_t>(nnz);
+  *v1 = sa.take<int32_t>(nnz);
+  *hist = sa.take<int32_t>(kRadix * ceil_div(nnz, kTile));
+  *flags = sa.take<unsigned>(1);
+}
+
 svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
                          const int32_t* cols, cudaStream_t s, svt_pattern** out) {
   if (!out) return fail(SVT_ERR_ARG, "pattern: null output handle");
@@ -237,25 +263,21 @@ svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
 
   // One allocation for the persistent arrays.
   Arena a;
-  auto layout = [&](Arena& ar, svt_pattern& p) {
-    p.row_ptr = ar.take<int32_t>(m + 1);
-    p.col_idx = ar.take<int32_t>(nnz);
-    p.csr_src = ar.take<int32_t>(nnz);
-    p.col_ptr = ar.take<int32_t>(n + 1);
-    p.row_idx = ar.take<int32_t>(nnz);
-    p.perm = ar.take<int32_t>(nnz);
-    p.csr_row = ar.take<int32_t>(nnz);
-    p.chunk = chunk_size(nnz > 0 ? nnz : 1);
-    p.nchunks = ceil_div(nnz, p.chunk);
-    p.chunk_row_csr = ar.take<int32_t>(p.nchunks);
-    p.chunk_row_csc = ar.take<int32_t>(p.nchunks);
-  };
+  auto layout = [&](Arena& ar, svt_pattern& p) { pattern_layout(ar, m, n, nnz, &p); };
   svt_pattern probe;
   layout(a, probe);
-  void* blk = nullptr;
-  SVT_CUDA(cudaMalloc(&blk, a.off));
   svt_pattern* p = new svt_pattern;
-  p->m = m; p->n = n; p->nnz = nnz; p->block = blk;
+  void* blk = nullptr;
+  if (current_workspace()) {  // a slice of the caller's workspace, released with the pattern
+    const svt_status st = p->ws_block.alloc(a.off, s);
+    if (st < 0) { delete p; return st; }
+    blk = p->ws_block.ptr;
+  } else {
+    const cudaError_t e = cudaMalloc(&blk, a.off);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMalloc(pattern)", __FILE__, __LINE__); }
+    p->block = blk;
+  }
+  p->m = m; p->n = n; p->nnz = nnz;
   Arena real; real.base = (char*)blk; real.cap = a.off;
   layout(real, *p);
 
@@ -271,24 +293,17 @@ svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   }
 
   // Scratch: two key/value buffer pairs, a histogram, a flags word.
-  const int64_t ntiles = ceil_div(nnz, kTile);
-  Arena sa;
-  uint64_t* k0 = sa.take<uint64_t>(nnz);
-  uint64_t* k1 = sa.take<uint64_t>(nnz);
-  int32_t* v0 = sa.take<int32_t>(nnz);
-  int32_t* v1 = sa.take<int32_t>(nnz);
-  int32_t* hist = sa.take<int32_t>(kRadix * ntiles);
-  unsigned* flags = sa.take<unsigned>(1);
+  uint64_t *k0, *k1;
+  int32_t *v0, *v1, *hist;
+  unsigned* flags;
   DeviceBlock scratch;
   {
-    svt_status st = scratch.alloc(sa.off, s);
+    svt_status st = scratch.alloc(pattern_scratch_bytes(nnz), s);
     if (st < 0) return cleanup(st);
   }
-  sa.base = (char*)scratch.ptr; sa.off = 0;
-  k0 = sa.take<uint64_t>(nnz); k1 = sa.take<uint64_t>(nnz);
-  v0 = sa.take<int32_t>(nnz); v1 = sa.take<int32_t>(nnz);
-  hist = sa.take<int32_t>(kRadix * ntiles);
-  flags = sa.take<unsigned>(1);
+  Arena sa;
+  sa.base = (char*)scratch.ptr;
+  scratch_layout(sa, nnz, &k0, &k1, &v0, &v1, &hist, &flags);
 
   auto run = [&]() -> svt_status {
     SVT_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
@@ -339,6 +354,31 @@ svt_status build_pattern(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     return cleanup(st);
   }
   *out = p;
+  return SVT_OK;
+}
+
+size_t pattern_block_bytes(int64_t m, int64_t n, int64_t nnz) {
+  Arena a;
+  svt_pattern probe;
+  pattern_layout(a, m, n, nnz, &probe);
+  return a.off;
+}
+
+size_t pattern_scratch_bytes(int64_t nnz) {
+  if (nnz <= 0) return 0;
+  Arena a;
+  uint64_t *k0, *k1;
+  int32_t *v0, *v1, *hist;
+  unsigned* flags;
+  scratch_layout(a, nnz, &k0, &k1, &v0, &v1, &hist, &flags);
+  return a.off;
+}
+
+svt_status launch_chunk_rows(int64_t nrows, int64_t C, int64_t nchunks, const int32_t* ptr,
+                             int32_t* out, cudaStream_t s) {
+  if (nchunks <= 0) return SVT_OK;
+  k_chunk_rows<<<grid_for(nchunks, 256), 256, 0, s>>>(nrows, C, nchunks, ptr, out);
+  SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <vector>
 
@@ -292,6 +293,9 @@ struct Work {
   // Non-null: this CSR copy of Y is stale (the fused update wrote only the CSC copy);
   // r4svd_run refreshes it from y_csc before its first CSR product and clears it.
   T* y_csr_stale = nullptr;
+  // Set when both full copies of Y are stale (the update wrote the sparse rest and the
+  // dense core instead): r4svd_run calls it before its first product with Y and clears it.
+  std::function<svt_status()> refresh_y;
   // Recycled iterations replay the eigen phase as a captured graph (two graphs: the basis
   // and B^T buffers alternate); host_pin is page-locked host memory of pin_doubles()
   // doubles for the graph's copies.  Off unless the caller provides host_pin.
@@ -651,7 +655,11 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
       SVT_TRY(launch_gaussian<T>(P.seed, iter, (uint32_t)blocks, n, w, W.Om, W.ldw, st));
     }
     ++blocks;
-    if (W.y_csr_stale) {
+    if (W.refresh_y) {
+      SVT_PROF("assemble_y", (double)z * (4 + 2 * sv) + (double)z * (4 + 2 * sv), st);
+      SVT_TRY(W.refresh_y());
+      W.refresh_y = nullptr;
+    } else if (W.y_csr_stale) {
       SVT_PROF("scatter_csr", (double)z * (4 + 2 * sv), st);
       SVT_TRY(launch_scatter<T>(z, p->perm, y_csc, W.y_csr_stale, st));
       W.y_csr_stale = nullptr;

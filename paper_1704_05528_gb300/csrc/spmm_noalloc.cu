@@ -16,8 +16,11 @@
 //    has to start at zero (each call writes every scratch word before reading it), but
 //    calls that overlap on the GPU (other threads or other streams) race on it;
 //  - the first call on a device looks up the array's device address there
-//    (cudaGetSymbolAddress, with that device current) and caches it; make that first
-//    call before starting any stream capture.
+//    (cudaGetSymbolAddress, with that device current) and caches it for the process; a
+//    cudaDeviceReset would leave that cached address stale, so resetting a device while
+//    this library is in use is not supported;
+//  - like svt_spmm, the call waits for its stream before returning, so it cannot be
+//    recorded into a stream capture.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,6 +28,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "solver.cuh"
 
 namespace svt {
 namespace {
@@ -93,7 +97,12 @@ extern "C" svt_status svt_spmm_noalloc(const svt_pattern* p, int precision, int 
     }
     return SVT_OK;
   };
-  SVT_TRY(precision == SVT_FP64 ? run(double(0)) : run(float(0)));
+  {
+    // the product's kernels, timed as one class when the library's profiler is on
+    SVT_PROF(transpose ? "api_spmm_csc" : "api_spmm_csr",
+             spmm_bytes(z, rows_out, transpose ? p->m : p->n, w, elem), s);
+    SVT_TRY(precision == SVT_FP64 ? run(double(0)) : run(float(0)));
+  }
   SVT_CUDA(cudaStreamSynchronize(s));
   return SVT_OK;
 }

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dense_core.cuh"
 #include "kernels.cuh"
 #include "solver.cuh"
 
@@ -84,7 +85,30 @@ bool is_device_pointer(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+static thread_local Workspace* g_ws = nullptr;
+Workspace* current_workspace() { return g_ws; }
+WorkspaceScope::WorkspaceScope(void* base, size_t bytes) : prev(g_ws) {
+  ws.base = static_cast<char*>(base);
+  ws.cap = bytes;
+  g_ws = base ? &ws : prev;
+}
+WorkspaceScope::~WorkspaceScope() { g_ws = prev; }
+
 svt_status DeviceBlock::alloc(size_t bytes, cudaStream_t s) {
+  release();
+  stream = s;
+  if (Workspace* w = g_ws) {
+    const size_t off = (size_t)round_up((int64_t)w->top, 256);
+    const size_t len = (size_t)round_up((int64_t)(bytes > 0 ? bytes : 256), 256);
+    if (off + len > w->cap)
+      return fail(SVT_ERR_ARG, "workspace of %zu bytes is too small (needs at least %zu)", w->cap, off + len);
+    ptr = w->base + off;
+    ws = w;
+    ws_prev_top = w->top;
+    ws_end = off + len;
+    w->top = ws_end;
+    return SVT_OK;
+  }
   static std::once_flag once;
   std::call_once(once, []() {
     // keep freed stream-ordered memory in the pool between calls
@@ -96,9 +120,37 @@ svt_status DeviceBlock::alloc(size_t bytes, cudaStream_t s) {
     }
     cudaGetLastError();
   });
-  stream = s;
   SVT_CUDA(cudaMallocAsync(&ptr, bytes > 0 ? bytes : 256, s));
   return SVT_OK;
+}
+
+// Page-locked host buffers for the solver's small device-to-host copies, kept for reuse
+// by later solves (a solve takes one while it runs).
+namespace {
+std::mutex g_pin_mu;
+std::vector<std::pair<void*, size_t>> g_pin_free;
+}  // namespace
+
+// *len receives the buffer's size (at least `bytes`), to be handed back to pinned_release.
+svt_status pinned_acquire(size_t bytes, void** out, size_t* len) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pin_free.size(); ++i)
+      if (g_pin_free[i].second >= bytes) {
+        *out = g_pin_free[i].first;
+        *len = g_pin_free[i].second;
+        g_pin_free.erase(g_pin_free.begin() + (int64_t)i);
+        return SVT_OK;
+      }
+  }
+  *len = std::max<size_t>(bytes, 64 * 1024);
+  SVT_CUDA(cudaMallocHost(out, *len));
+  return SVT_OK;
+}
+
+void pinned_release(void* p, size_t len) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.emplace_back(p, len);
 }
 
 // profiler state shared with solver.cuh
@@ -110,6 +162,12 @@ std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
 
 namespace {
+
+// Rows with at least this fraction of n observed entries form the dense core (automatic
+// choice).  On the tensor cores a core row costs its whole panel row (A read, Y read and
+// written: 12 bytes per column); on the gather path each of its entries costs one
+// gathered row of U (4r bytes from L2), so rows this full are far cheaper in the core.
+constexpr double kCoreMinFrac = 0.1;
 
 // The evaluation set of svt_complete_eval on the device: its own sorted pattern, the
 // values in that pattern's CSR order, and a zero Y for the sampled pass (delta = 0).
@@ -143,6 +201,86 @@ struct EvalSet {
     return SVT_OK;
   }
 };
+
+// The solve's own device arrays next to the R4SVD work buffers: A and Y in both orders, a
+// second B^T that the fused update fills while the solver still reads the current one, the
+// fused update's block sums, and the dense core (binary32) when the plan has one.
+template <typename T>
+struct SolveBufs {
+  T *a_csr = nullptr, *y_csr = nullptr, *a_csc = nullptr, *bt_alt = nullptr;
+  double* fpart = nullptr;
+  int64_t ldb_alt = 0;
+  DenseCore core;
+  int32_t* core_src = nullptr;
+  void layout(Arena& ar, int64_t m, int64_t n, int64_t nnz, int r_cap, const CorePlan& plan) {
+    ldb_alt = ld_of(r_cap);
+    a_csr = ar.take<T>(nnz);
+    y_csr = ar.take<T>(nnz);
+    a_csc = ar.take<T>(nnz);
+    bt_alt = ar.take<T>(n * ldb_alt);
+    fpart = ar.take<double>(update_recycle_scratch(nnz));
+    if (plan.rd > 0) {
+      core_layout(ar, plan, m, n, r_cap, &core);
+      core_src = ar.take<int32_t>(nnz);
+    }
+  }
+};
+
+// Peak bytes a solve takes from a caller workspace, replaying its allocations in order:
+// the inputs' device copies (counted whether or not the inputs are host memory), the
+// pattern with its sort scratch, the evaluation set with its pattern and scratch, the solve
+// arena (with the largest core the plan could choose), and the staging of host outputs.
+template <typename T>
+size_t complete_ws_bytes(int64_t m, int64_t n, int64_t nnz, int64_t n_eval, int32_t cap,
+                         const svt_options* opt, const Params& P) {
+  auto blk = [](size_t bytes) { return (size_t)round_up((int64_t)(bytes > 0 ? bytes : 256), 256); };
+  size_t in = 0;
+  if (nnz > 0) {
+    Arena a;
+    a.take<int32_t>(nnz); a.take<int32_t>(nnz); a.take<T>(nnz);
+    in = blk(a.off);
+  }
+  const size_t pat = blk(pattern_block_bytes(m, n, nnz));
+  const size_t pat_scr = nnz > 0 ? blk(pattern_scratch_bytes(nnz)) : 0;
+  size_t ev = 0, ev_pat = 0, ev_scr = 0;
+  if (n_eval > 0) {
+    Arena e;
+    e.take<int32_t>(n_eval); e.take<int32_t>(n_eval);
+    e.take<T>(n_eval); e.take<T>(n_eval); e.take<T>(n_eval);
+    ev = blk(e.off);
+    ev_pat = blk(pattern_block_bytes(m, n, n_eval));
+    ev_scr = blk(pattern_scratch_bytes(n_eval));
+  }
+  size_t main = 0;
+  if (nnz > 0) {
+    CorePlan bound;
+    if (sizeof(T) == 4 && opt->core_rows != 0)
+      bound = core_plan_bound(m, n, nnz, opt->core_rows, kCoreMinFrac);
+    svt_pattern fake;
+    fake.m = m; fake.n = n; fake.nnz = nnz;
+    Work<T> W;
+    W.P = P; W.pat = &fake;
+    SolveBufs<T> B;
+    Arena a;
+    B.layout(a, m, n, nnz, P.r_cap, bound);
+    W.layout(a);
+    main = blk(a.off);
+  }
+  const size_t out = blk((size_t)std::max(m, n) * (size_t)std::max(cap, 1) * sizeof(double));
+  return in + pat + std::max(pat_scr, ev + ev_pat + std::max(ev_scr, main + out));
+}
+
+// Bytes svt_r4svd takes from a caller workspace: its work buffers.
+template <typename T>
+size_t r4svd_ws_bytes(int64_t m, int64_t n, int64_t nnz, const Params& P) {
+  svt_pattern fake;
+  fake.m = m; fake.n = n; fake.nnz = nnz;
+  Work<T> W;
+  W.P = P; W.pat = &fake;
+  Arena a;
+  W.layout(a);
+  return (size_t)round_up((int64_t)(a.off > 0 ? a.off : 256), 256);
+}
 
 template <typename T>
 svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
@@ -217,38 +355,38 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   // page-locked host words for the copies inside the captured eigen phase
   struct HostPin {
     void* p = nullptr;
+    size_t bytes = 0;
     cudaStream_t s = nullptr;
     ~HostPin() {
       if (!p) return;
       cudaStreamSynchronize(s);  // a graph launched ahead may still copy into it
-      cudaFreeHost(p);
+      pinned_release(p, bytes);
     }
   } pin;
   pin.s = st;
-  SVT_CUDA(cudaMallocHost(&pin.p, Work<T>::pin_doubles(P.r_cap) * sizeof(double)));
+  SVT_TRY(pinned_acquire(Work<T>::pin_doubles(P.r_cap) * sizeof(double), &pin.p, &pin.bytes));
   Work<T> W;
   W.P = P; W.pat = pat; W.s = st;
   W.host_pin = static_cast<double*>(pin.p);
-  // A and Y in both orders, and a second B^T that the fused update fills while the
-  // solver still reads the current one
-  const int64_t ldb_alt = ld_of(P.r_cap);
-  auto take_own = [&](Arena& ar, T** a_csr_, T** y_csr_, T** a_csc_, T** bt_alt_, double** fpart_) {
-    *a_csr_ = ar.take<T>(nnz);
-    *y_csr_ = ar.take<T>(nnz);
-    *a_csc_ = ar.take<T>(nnz);
-    *bt_alt_ = ar.take<T>(n * ldb_alt);
-    *fpart_ = ar.take<double>(update_recycle_scratch(nnz));
-  };
-  T *a_csr, *y_csr, *a_csc, *bt_alt;
-  double* fpart;
+  // binary32: the fullest rows may form a dense core updated on the tensor cores
+  CorePlan cplan;
+  if constexpr (sizeof(T) == 4) {
+    if (opt->core_rows != 0 && P.r_cap >= 1) SVT_TRY(core_plan(pat, opt->core_rows, kCoreMinFrac, st, &cplan));
+  }
+  SolveBufs<T> B;
   Arena a;
-  take_own(a, &a_csr, &y_csr, &a_csc, &bt_alt, &fpart);
+  B.layout(a, m, n, nnz, P.r_cap, cplan);
   W.layout(a);
   DeviceBlock wblk;
   SVT_TRY(wblk.alloc(a.off, st));
   Arena b; b.base = (char*)wblk.ptr;
-  take_own(b, &a_csr, &y_csr, &a_csc, &bt_alt, &fpart);
+  B.layout(b, m, n, nnz, P.r_cap, cplan);
   W.layout(b);
+  const int64_t ldb_alt = B.ldb_alt;
+  T *a_csr = B.a_csr, *y_csr = B.y_csr, *a_csc = B.a_csc, *bt_alt = B.bt_alt;
+  double* fpart = B.fpart;
+  DenseCore& core = B.core;
+  int32_t* core_src = B.core_src;
   SVT_CUDA(cudaMemsetAsync(W.flags, 0, kFlagWords * sizeof(unsigned), st));
 
   // P_Lambda(A) in CSR order; reject non-finite values.
@@ -292,6 +430,10 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
   res->spec_norm = s2;
   SVT_TRY(scale_copy<T>(nnz, a_csr, (double)k0 * delta, y_csr, st));
   SVT_TRY(launch_gather<T>(nnz, pat->perm, y_csr, W.y_csc, st));
+  bool core_active = false;  // Y lives in the sparse rest and the core panel
+  if constexpr (sizeof(T) == 4) {
+    if (cplan.rd > 0) SVT_TRY(core_build(pat, cplan, a_csc, core_src, st, &core));
+  }
   double normY2 = 0.0;
   SVT_TRY(sumsq<T>(nnz, y_csr, W.dsc + 4, W.part, st));
   SVT_CUDA(cudaMemcpyAsync(&normY2, W.dsc + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -329,7 +471,36 @@ svt_status complete_impl(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
     // B^T = Y^T U[:, :s_next] for that call.
     const int s_next = P.recycle == SVT_RECYCLE_ALL ? r : P.recycle == SVT_RECYCLE_KEPT ? k : 0;
     fused = s_next > 0 && update_recycle_fits<T>(s_next, nnz);
-    if (fused) {
+    bool use_core = false;
+    if constexpr (sizeof(T) == 4) use_core = fused && cplan.rd > 0 && core_fits(s_next, k);
+    if (core_active && !use_core) {  // back to the full copies of Y
+      SVT_PROF("assemble_y", 2.0 * (double)nnz * (4 + 2 * sizeof(T)), st);
+      if constexpr (sizeof(T) == 4) SVT_TRY(core_assemble(pat, core, y_csr, W.y_csc, st));
+      core_active = false;
+      W.refresh_y = nullptr;
+      W.y_csr_stale = nullptr;
+    }
+    if (use_core) {
+      if constexpr (sizeof(T) == 4) {
+        if (!core_active) {
+          SVT_TRY(core_enter(pat, W.y_csc, st, &core));
+          core_active = true;
+        }
+        {
+          SVT_PROF("update_recycled", recycle_bytes(core.rest.nnz, m, n, k, s_next, (int)sizeof(T)), st);
+          SVT_TRY(update_recycle<T>(&core.rest, Qnext, W.ldq, s_next, W.Wk, W.ldk, k, core.a_rest,
+                                    core.y_rest, delta, bt_alt, ldb_alt, W.dsc + 5, core.upd_part,
+                                    W.flags, core.upd_scratch, st));
+        }
+        {
+          SVT_PROF("update_core", (double)cplan.core_nnz * (4 + 3 * sizeof(T)), st);
+          SVT_TRY(core_update(core, Qnext, W.ldq, s_next, W.Wk, W.ldk, k, delta, bt_alt, ldb_alt,
+                              W.dsc + 5, W.flags, W.flags + 4, st));
+        }
+        W.y_csr_stale = nullptr;
+        W.refresh_y = [&]() { return core_assemble(pat, core, y_csr, W.y_csc, W.s); };
+      }
+    } else if (fused) {
       SVT_PROF("update_recycled", recycle_bytes(nnz, m, n, k, s_next, (int)sizeof(T)), st);
       SVT_TRY(update_recycle<T>(pat, Qnext, W.ldq, s_next, W.Wk, W.ldk, k, a_csc, W.y_csc, delta,
                                 bt_alt, ldb_alt, W.dsc + 5, fpart, W.flags, W.spmm_scr, st));
@@ -478,7 +649,7 @@ svt_status r4svd_impl(const svt_pattern* p, const T* y_csr, const T* U_prev, int
 }  // namespace svt
 
 // ====================================================================== C ABI
-extern "C" int svt_abi_version(void) { return 2; }
+extern "C" int svt_abi_version(void) { return 3; }
 
 extern "C" void svt_default_options(svt_options* o) {
   if (!o) return;
@@ -490,6 +661,8 @@ extern "C" void svt_default_options(svt_options* o) {
   o->precision = SVT_FP64;
   o->recycle = SVT_RECYCLE_ALL;
   o->stop = SVT_STOP_RESIDUAL;
+  o->core_rows = -1;
+  o->reserved = 0;
   o->beta = 0.95;
   o->eps_thr0 = 0.9;
   o->seed = 0x5EEDull;
@@ -620,12 +793,37 @@ extern "C" svt_status svt_sampled_update_recycle(const svt_pattern* p, int preci
   return SVT_OK;
 }
 
+extern "C" size_t svt_r4svd_workspace_size(int64_t m, int64_t n, int64_t nnz, const svt_options* opt) {
+  using namespace svt;
+  Params P;
+  if (!opt || m <= 0 || n <= 0 || nnz < 0 || make_params(m, n, opt, &P) != SVT_OK) return 0;
+  return opt->precision == SVT_FP64 ? r4svd_ws_bytes<double>(m, n, nnz, P) : r4svd_ws_bytes<float>(m, n, nnz, P);
+}
+
+extern "C" size_t svt_workspace_size(int64_t m, int64_t n, int64_t nnz, int64_t n_eval, int32_t cap,
+                                     const svt_options* opt) {
+  using namespace svt;
+  Params P;
+  if (!opt || m <= 0 || n <= 0 || nnz < 0 || n_eval < 0 || make_params(m, n, opt, &P) != SVT_OK)
+    return 0;
+  return opt->precision == SVT_FP64 ? complete_ws_bytes<double>(m, n, nnz, n_eval, cap, opt, P)
+                                    : complete_ws_bytes<float>(m, n, nnz, n_eval, cap, opt, P);
+}
+
 extern "C" svt_status svt_r4svd(const svt_pattern* p, const void* y_csr, const void* U_prev,
                                 int64_t ld_prev, int32_t s, double eps_thr, uint32_t iter,
                                 const svt_options* opt, void* U, int64_t ldu, double* S, void* V,
-                                int64_t ldv, int32_t* r_out, double* eps_out, int32_t* blocks_out) {
+                                int64_t ldv, int32_t* r_out, double* eps_out, int32_t* blocks_out,
+                                void* workspace, size_t ws_bytes) {
   using namespace svt;
   if (!p || !opt || (p->nnz > 0 && !y_csr)) return fail(SVT_ERR_ARG, "r4svd: bad arguments");
+  if (workspace) {
+    const size_t need = svt_r4svd_workspace_size(p->m, p->n, p->nnz, opt);
+    if (need == 0 || ws_bytes < need)
+      return fail(SVT_ERR_ARG, "r4svd: workspace of %zu bytes is below the %zu bytes of "
+                               "svt_r4svd_workspace_size", ws_bytes, need);
+  }
+  WorkspaceScope scope(workspace, ws_bytes);
   if (opt->precision == SVT_FP64)
     return r4svd_impl<double>(p, (const double*)y_csr, (const double*)U_prev, ld_prev, s, eps_thr,
                               iter, opt, (double*)U, ldu, S, (double*)V, ldv, r_out, eps_out,
@@ -640,9 +838,10 @@ extern "C" svt_status svt_complete(int64_t m, int64_t n, int64_t nnz, const int3
                                    const int32_t* cols, const void* vals, double tau, double delta,
                                    double tol, int32_t maxit, const svt_options* opt, double* U,
                                    double* S, double* V, int32_t cap, svt_result* res,
-                                   svt_iter_log* log, int32_t log_cap) {
+                                   svt_iter_log* log, int32_t log_cap, void* workspace,
+                                   size_t ws_bytes) {
   return svt_complete_eval(m, n, nnz, rows, cols, vals, 0, nullptr, nullptr, nullptr, tau, delta,
-                           tol, maxit, opt, U, S, V, cap, res, log, log_cap);
+                           tol, maxit, opt, U, S, V, cap, res, log, log_cap, workspace, ws_bytes);
 }
 
 extern "C" svt_status svt_complete_eval(int64_t m, int64_t n, int64_t nnz, const int32_t* rows,
@@ -651,7 +850,8 @@ extern "C" svt_status svt_complete_eval(int64_t m, int64_t n, int64_t nnz, const
                                         const void* eval_vals, double tau, double delta,
                                         double tol, int32_t maxit, const svt_options* opt,
                                         double* U, double* S, double* V, int32_t cap,
-                                        svt_result* res, svt_iter_log* log, int32_t log_cap) {
+                                        svt_result* res, svt_iter_log* log, int32_t log_cap,
+                                        void* workspace, size_t ws_bytes) {
   using namespace svt;
   if (!res) return fail(SVT_ERR_ARG, "complete: null result");
   memset(res, 0, sizeof(*res));
@@ -664,6 +864,17 @@ extern "C" svt_status svt_complete_eval(int64_t m, int64_t n, int64_t nnz, const
   if (nnz > 0 && (!rows || !cols || !vals)) return fail(SVT_ERR_ARG, "complete: null input array");
   if (n_eval < 0 || (n_eval > 0 && (!eval_rows || !eval_cols || !eval_vals)))
     return fail(SVT_ERR_ARG, "complete: bad evaluation set");
+  if (workspace) {  // checked before any work is queued
+    const size_t need = svt_workspace_size(m, n, nnz, n_eval, cap, opt);
+    if (need == 0) {
+      Params P;
+      return make_params(m, n, opt, &P);  // sets the message of the invalid option
+    }
+    if (ws_bytes < need)
+      return fail(SVT_ERR_ARG, "complete: workspace of %zu bytes is below the %zu bytes of "
+                               "svt_workspace_size", ws_bytes, need);
+  }
+  WorkspaceScope scope(workspace, ws_bytes);
   svt_status st;
   if (opt->precision == SVT_FP64)
     st = complete_impl<double>(m, n, nnz, rows, cols, (const double*)vals, tau, delta, tol, maxit,

@@ -25,38 +25,6 @@ constexpr int kRedBlocksPerSm = 8;
 
 int red_blocks() { return num_sms() * kRedBlocksPerSm; }
 
-template <typename T>
-struct SumAcc;
-
-template <>
-struct SumAcc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ void add_sq(double x) { s = fma(x, x, s); }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
-// hi + lo holds the sum.  Knuth's TwoSum gives the exact error of hi + p, and fma gives
-// the exact error of a rounded product; the intrinsics keep the compiler from fusing
-// the steps that must round separately.
-template <>
-struct SumAcc<float> {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add2(float p, float e) {
-    const float t = __fadd_rn(hi, p);
-    const float z = __fsub_rn(t, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
-    hi = t;
-  }
-  __device__ __forceinline__ void add(float x) { add2(x, 0.f); }
-  __device__ __forceinline__ void add_sq(float x) {
-    const float p = __fmul_rn(x, x);
-    add2(p, fmaf(x, x, -p));
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 template <typename T, int VEC>
 __device__ __forceinline__ void load_v(const T* p, T (&v)[VEC]) {
   if constexpr (VEC == 1) {

@@ -114,23 +114,36 @@ def test_forward_only_and_uncertified_kept_set(svt):
         _call(svt, w, 1e-3, delta, 2, precision="fp64", r_max=2, t=2, dt=1)
 
 
-def test_autograd_function(svt):
+@pytest.mark.parametrize("device", ["cpu", "cuda"])
+def test_autograd_function(svt, device):
+    """SVTUnrolled returns X^(T) on the held-out entries; the loss is computed in torch and
+    its gradient flows through svt_unrolled_backward.  With host or device tensors it must
+    reproduce svt_unrolled_grad (the held-out MSE and its gradient) exactly."""
     import torch
     w = workloads.random_lowrank(36, 36, 2, 0.5, seed=7, n_hold=100)
-    problem = dict(m=w.m, n=w.n, rows=w.rows, cols=w.cols, held_rows=w.held_rows,
-                   held_cols=w.held_cols, held_vals=w.held_vals, steps=4,
+    idx = (lambda a: torch.from_numpy(a).cuda()) if device == "cuda" else (lambda a: a)
+    problem = dict(m=w.m, n=w.n, rows=idx(w.rows), cols=idx(w.cols), held_rows=idx(w.held_rows),
+                   held_cols=idx(w.held_cols), steps=4,
                    options=dict(checkpoint_every=2, cg_tol=1e-12, precision="fp64", seed=w.seed))
-    vals = torch.tensor(w.vals, dtype=torch.float64, requires_grad=True)
+    vals = torch.tensor(w.vals, dtype=torch.float64, device=device, requires_grad=True)
     tau = torch.tensor(2.0 * np.sqrt(w.m * w.n), dtype=torch.float64, requires_grad=True)
     delta = torch.tensor(1.3, dtype=torch.float64, requires_grad=True)
-    loss = svt.SVTUnrolled.apply(vals, tau, delta, problem)
+    x = svt.SVTUnrolled.apply(vals, tau, delta, problem)
+    assert x.device.type == device and x.shape == (w.held_rows.size,)
+    held = torch.tensor(w.held_vals, dtype=torch.float64, device=device)
+    loss = ((x - held) ** 2).mean()
     (3.0 * loss).backward()
     direct = svt.unrolled_grad(w.m, w.n, w.rows, w.cols, w.vals, w.held_rows, w.held_cols, w.held_vals,
                                float(tau), float(delta), 4, **problem["options"])
-    assert loss.item() == direct["loss"]
-    assert np.array_equal(vals.grad.numpy(), 3.0 * direct["grad_vals"])
-    assert tau.grad.item() == 3.0 * direct["grad_tau"]
-    assert delta.grad.item() == 3.0 * direct["grad_delta"]
+    assert np.array_equal(x.detach().cpu().numpy(), direct["x_held"])
+    assert abs(loss.item() - direct["loss"]) <= 1e-14 * direct["loss"]
+    np.testing.assert_allclose(vals.grad.cpu().numpy(), 3.0 * direct["grad_vals"], rtol=1e-12, atol=1e-18)
+    assert abs(tau.grad.item() - 3.0 * direct["grad_tau"]) <= 1e-12 * abs(direct["grad_tau"])
+    assert abs(delta.grad.item() - 3.0 * direct["grad_delta"]) <= 1e-12 * abs(direct["grad_delta"])
+    # no gradient wanted: the forward keeps no tape and costs only the forward pass
+    with torch.no_grad():
+        x2 = svt.SVTUnrolled.apply(vals, tau, delta, problem)
+    assert torch.equal(x2, x.detach())
 
 
 # The full-size differentiable workload: 2000 x 2000 rank 20, 10% observed, 40,000 held-out
@@ -175,3 +188,37 @@ def test_unrolled2000_fp32_gradient(svt):
                        (g32["grad_tau"], fd_tau), (g32["grad_delta"], fd_delta),
                        (report["gdir"][0], fd_vals)):
         assert _scalar_close(got, exact, 1e-4), report
+
+
+def test_unrolled2000_through_autograd_on_the_device(svt):
+    """The 2000 x 2000 workload in binary32 through SVTUnrolled with CUDA tensors: the
+    gradient equals svt_unrolled_grad's (the loss's gradient on X^(T) is formed in torch
+    instead of in the library, so agreement is to rounding), and a forward-only call
+    (no tape) takes the forward time, well under forward + backward."""
+    import time
+    import torch
+    w = workloads.make("unrolled2000")
+    d = lambda a: torch.from_numpy(a).cuda()
+    problem = dict(m=w.m, n=w.n, rows=d(w.rows), cols=d(w.cols), held_rows=d(w.held_rows),
+                   held_cols=d(w.held_cols), steps=20,
+                   options=dict(checkpoint_every=5, r_max=200, precision="mixed", seed=w.seed))
+    vals = torch.tensor(w.vals, dtype=torch.float32, device="cuda", requires_grad=True)
+    held = d(w.held_vals)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x = svt.SVTUnrolled.apply(vals, w.tau, w.delta, problem)
+    loss = ((x - held) ** 2).mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        x_fwd = svt.SVTUnrolled.apply(vals, w.tau, w.delta, problem)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    direct = _call(svt, w, w.tau, w.delta, 20, precision="mixed", checkpoint_every=5, r_max=200)
+    print(f"\nunrolled2000 through autograd: forward + backward {t_full:.3f} s, forward only {t_fwd:.3f} s")
+    assert torch.equal(x_fwd, x.detach())
+    assert _rel(x.detach().cpu().numpy(), direct["x_held"]) == 0.0
+    assert _rel(vals.grad.double().cpu().numpy(), direct["grad_vals"]) < 1e-6
+    assert t_fwd < 0.75 * t_full

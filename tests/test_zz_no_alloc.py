@@ -6,6 +6,8 @@ would stall a latency-critical loop).  It must give the result of the ordinary e
 point, call after call, even though every call reuses the same fixed scratch array.
 This file is collected last; it also passes on its own in a fresh process.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -81,3 +83,72 @@ def test_noalloc_takes_column_slices_of_wider_arrays(env, prec, tol):
             err = (ob[:, :width] - ref).norm().item() / max(ref.norm().item(), 1e-300)
             assert err <= tol
             assert torch.isnan(ob[:, width:]).all()
+
+
+def _default_pool_used(torch):
+    """(current, high-water) bytes in use in the device's default stream-ordered pool,
+    read through the driver API; None where the driver library cannot be loaded."""
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+    except OSError:
+        return None
+    pool = ctypes.c_void_p()
+    if cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), ctypes.c_int(torch.cuda.current_device())) != 0:
+        return None
+    used_current, used_high = 7, 8  # CU_MEMPOOL_ATTR_USED_MEM_CURRENT / _HIGH
+    cur, high = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    if cu.cuMemPoolGetAttribute(pool, used_current, ctypes.byref(cur)) != 0:
+        return None
+    if cu.cuMemPoolGetAttribute(pool, used_high, ctypes.byref(high)) != 0:
+        return None
+    return cu, pool, cur.value, high.value
+
+
+def test_noalloc_allocates_no_device_memory(env):
+    """The point of the entry point: repeated calls leave torch's allocator, the device's
+    free memory and the default stream-ordered pool (whose high-water mark would catch an
+    allocation freed before the call returns) exactly where they were."""
+    svt, torch = env
+    rng = np.random.default_rng(10)
+    P = _pattern(svt, rng, 700, 450, 40000)
+    y = torch.from_numpy(rng.standard_normal(P.nnz)).to(device="cuda", dtype=torch.float32)
+    Wn = torch.from_numpy(rng.standard_normal((P.n, 12))).to(device="cuda", dtype=torch.float32)
+    Wm = torch.from_numpy(rng.standard_normal((P.m, 12))).to(device="cuda", dtype=torch.float32)
+    on = torch.empty((P.m, 12), device="cuda", dtype=torch.float32)
+    ot = torch.empty((P.n, 12), device="cuda", dtype=torch.float32)
+    # first calls: address lookup, and the kernels' code loaded on first launch
+    svt.spmm_noalloc(P, y, Wn, on, precision="mixed")
+    svt.spmm_noalloc(P, y, Wm, ot, transpose=True, precision="mixed")
+    torch.cuda.synchronize()
+    pool = _default_pool_used(torch)
+    if pool is not None:
+        cu, handle, cur0, _ = pool
+        # restart the pool's high-water mark from the bytes in use now
+        assert cu.cuMemPoolSetAttribute(handle, 8, ctypes.byref(ctypes.c_uint64(0))) == 0
+    torch_before = torch.cuda.memory_allocated()
+    free_before = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        svt.spmm_noalloc(P, y, Wn, on, precision="mixed")
+        svt.spmm_noalloc(P, y, Wm, ot, transpose=True, precision="mixed")
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == torch_before
+    assert torch.cuda.mem_get_info()[0] == free_before
+    if pool is not None:
+        _, _, cur1, high1 = _default_pool_used(torch)
+        assert cur1 == cur0 and high1 == cur0
+
+
+def test_noalloc_rejects_short_operands_on_the_host(env):
+    """The C entry point cannot see buffer sizes, so the binding refuses a W with the
+    wrong number of rows or a y of the wrong length before anything is queued."""
+    svt, torch = env
+    rng = np.random.default_rng(11)
+    P = _pattern(svt, rng, 300, 200, 5000)
+    y = torch.zeros(P.nnz, device="cuda", dtype=torch.float64)
+    out = torch.zeros((P.m, 4), device="cuda", dtype=torch.float64)
+    with pytest.raises(ValueError):
+        svt.spmm_noalloc(P, y, torch.zeros((P.n - 1, 4), device="cuda", dtype=torch.float64), out)
+    with pytest.raises(ValueError):
+        svt.spmm_noalloc(P, y[:-1], torch.zeros((P.n, 4), device="cuda", dtype=torch.float64), out)
+    with pytest.raises(ValueError):
+        svt.spmm(P, y, torch.zeros((P.n, 4), device="cuda", dtype=torch.float64), transpose=True)
