@@ -523,6 +523,8 @@ def our_arm(args):
     # roofline of the dominant kernel class
     peaks, peak_src = load_peaks()
     sweeps = prof.pop("jacobi_sweeps", None)
+    # sub-steps of the dense core, timed inside the update_core class (not added to the total)
+    core_parts = {k: prof.pop(k) for k in list(prof) if k.startswith("core_")}
     events = {k: prof.pop(k)["launches"] for k in ("eig_start_oversize", "eig_start_rejected",
                                                    "eig_start_rejected_twice",
                                                    "eig_graph_unavailable") if k in prof}
@@ -595,6 +597,9 @@ def our_arm(args):
             "roofline": roofline,
             "spmm_block": narrow,
             "kernels": breakdown,
+            "core_parts": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1),
+                               "GB/s": round(v["bytes"] / max(v["ms"], 1e-12) / 1e6, 1)}
+                           for k, v in core_parts.items()} or None,
             "jacobi_sweeps_per_call": (sweeps["bytes"] / max(sweeps["launches"], 1)) if sweeps else None,
             "eig_start_events": events,
             "cpu_baseline": cpu,

@@ -12,6 +12,7 @@
 // chol_inv: one-block Cholesky G = R^T R of a small SPD matrix and R^-1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -96,6 +97,69 @@ k_gemm_tn_part(int64_t M, int p, int q, const TA* __restrict__ A, int64_t lda,
   if (a_0 < p && b_1 < q) P[(int64_t)a_0 * q + b_1] = (double)acc[1] + (double)lo[1];
   if (a_1 < p && b_0 < q) P[(int64_t)a_1 * q + b_0] = (double)acc[2] + (double)lo[2];
   if (a_1 < p && b_1 < q) P[(int64_t)a_1 * q + b_1] = (double)acc[3] + (double)lo[3];
+}
+
+// The binary32 case of k_gemm_tn_part with four times the work per thread: a 32 x 32
+// output tile per block of 64 threads, 4 x 4 outputs per thread (rows ty + 8a, columns
+// tx + 8b), so that each step reads 8 values from shared memory for 16 error-free products
+// (the same accumulation per output as k_gemm_tn_part).
+__global__ void __launch_bounds__(64)
+k_gemm_tn_part4(int64_t M, int p, int q, const float* __restrict__ A, int64_t lda,
+                const float* __restrict__ B, int64_t ldb, int64_t rows_per_split,
+                double* __restrict__ part, int symmetric) {
+  int ta = blockIdx.x, tb = blockIdx.y;
+  if (symmetric) {
+    const int T = (p + TN_TILE - 1) / TN_TILE;
+    int t = blockIdx.x;
+    ta = 0;
+    while (t >= T - ta) { t -= T - ta; ++ta; }
+    tb = ta + t;
+  }
+  __shared__ float As[TN_TILE][TN_TILE + 1];
+  __shared__ float Bs[TN_TILE][TN_TILE + 1];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int a0 = ta * TN_TILE, b0 = tb * TN_TILE;
+  const int64_t i_beg = (int64_t)blockIdx.z * rows_per_split;
+  int64_t i_end = i_beg + rows_per_split;
+  if (i_end > M) i_end = M;
+  float hi[4][4], lo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { hi[a][b] = 0.f; lo[a][b] = 0.f; }
+  for (int64_t i0 = i_beg; i0 < i_end; i0 += TN_TILE) {
+    for (int t = threadIdx.x; t < TN_TILE * TN_TILE; t += blockDim.x) {
+      const int rr = t / TN_TILE, cc = t % TN_TILE;
+      const int64_t i = i0 + rr;
+      const bool in = i < i_end;
+      As[rr][cc] = (in && a0 + cc < p) ? A[i * lda + a0 + cc] : 0.f;
+      Bs[rr][cc] = (in && b0 + cc < q) ? B[i * ldb + b0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TN_TILE; ++kk) {
+      float x[4], y[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[a] = As[kk][ty + 8 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) y[b] = Bs[kk][tx + 8 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dd_fma(x[a], y[b], hi[a][b], lo[a][b]);
+    }
+    __syncthreads();
+  }
+  double* P = part + (int64_t)blockIdx.z * p * q;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int ia = a0 + ty + 8 * a;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int jb = b0 + tx + 8 * b;
+      if (ia < p && jb < q) P[(int64_t)ia * q + jb] = (double)hi[a][b] + (double)lo[a][b];
+    }
+  }
 }
 
 // C[a][b] = sum_z part[z][a][b]; for a symmetric product the lower tiles read the
@@ -356,10 +420,21 @@ int grid_cap(int64_t work, int threads, int per_sm) {
 }  // namespace
 
 // Bound valid for every p' <= p, q' <= q: splits * p' * q' <= (4 SMs + tiles) * 32 * 32.
+// Splits of the binary32 kernel: about eight blocks of 64 threads per SM over the output
+// tiles, at least 32 rows per split, and a partial-sum buffer of at most kTn4PartDoubles.
+constexpr int64_t kTn4PartDoubles = int64_t(1) << 21;
+int tn4_splits(int64_t M, int p, int q, int64_t tiles) {
+  int64_t want = ceil_div((int64_t)num_sms() * 8, tiles);
+  want = std::min<int64_t>(want, ceil_div(M, 32));
+  want = std::min<int64_t>(want, kTn4PartDoubles / std::max<int64_t>((int64_t)p * q, 1));
+  return (int)std::max<int64_t>(want, 1);
+}
+
 size_t gemm_tn_scratch(int64_t M, int p, int q) {
   (void)M;
   const int64_t tiles = ceil_div(p > 0 ? p : 1, TN_TILE) * ceil_div(q > 0 ? q : 1, TN_TILE);
-  return (size_t)((int64_t)num_sms() * 4 + tiles + 1) * TN_TILE * TN_TILE;
+  const size_t old = (size_t)((int64_t)num_sms() * 4 + tiles + 1) * TN_TILE * TN_TILE;
+  return std::max<size_t>(old, (size_t)kTn4PartDoubles + (size_t)p * q);
 }
 
 template <typename TA, typename TB>
@@ -370,14 +445,20 @@ svt_status gemm_tn(int64_t M, int p, int q, const TA* A, int64_t lda, const TB* 
     for (int a = 0; a < p; ++a) SVT_CUDA(cudaMemsetAsync(C + (int64_t)a * ldc, 0, q * sizeof(double), s));
     return SVT_OK;
   }
-  const int splits = tn_splits(M, p, q);
-  const int64_t rows = round_up(ceil_div(M, splits), TN_TILE);
-  const int used = (int)ceil_div(M, rows);
   const int sym = (A == (const TA*)(const void*)B && p == q && lda == ldb) ? 1 : 0;
   const int64_t tp = ceil_div(p, TN_TILE);
+  const int64_t tiles = sym ? tp * (tp + 1) / 2 : tp * ceil_div(q, TN_TILE);
+  constexpr bool kF32 = sizeof(TA) == 4 && sizeof(TB) == 4;
+  const int splits = kF32 ? tn4_splits(M, p, q, tiles) : tn_splits(M, p, q);
+  const int64_t rows = round_up(ceil_div(M, splits), TN_TILE);
+  const int used = (int)ceil_div(M, rows);
   dim3 grid(sym ? (unsigned)(tp * (tp + 1) / 2) : (unsigned)tp,
             sym ? 1u : (unsigned)ceil_div(q, TN_TILE), (unsigned)used);
-  k_gemm_tn_part<TA, TB><<<grid, 256, 0, s>>>(M, p, q, A, lda, B, ldb, rows, part, sym);
+  if constexpr (kF32) {
+    k_gemm_tn_part4<<<grid, 64, 0, s>>>(M, p, q, (const float*)A, lda, (const float*)B, ldb, rows, part, sym);
+  } else {
+    k_gemm_tn_part<TA, TB><<<grid, 256, 0, s>>>(M, p, q, A, lda, B, ldb, rows, part, sym);
+  }
   SVT_LAUNCH_CHECK();
   launch_reduce_parts(p, q, used, part, C, ldc, sym, s);
   SVT_LAUNCH_CHECK();

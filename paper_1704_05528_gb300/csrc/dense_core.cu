@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "dense_core.cuh"
 #include "kernels.cuh"
+#include "solver.cuh"
 #include "tc_common.cuh"
 
 namespace svt {
@@ -166,23 +167,37 @@ __global__ void k_split_w(int64_t n, int k, const float* __restrict__ W, int64_t
 
 // TF32 parts of the core rows of U (m x r, ldu): UD (ldd x 128, K-major, columns j < k)
 // for the X product and UDt (npad x ldd, K-major, rows j < r) for the B^T product; zero in
-// padding slots and beyond k / r.
-__global__ void k_gather_ud(int64_t ldd, int k, int r, int npad, const int32_t* __restrict__ slot_row,
-                            const float* __restrict__ U, int64_t ldu, float* __restrict__ ud_hi,
-                            float* __restrict__ ud_lo, float* __restrict__ udt_hi,
-                            float* __restrict__ udt_lo) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ldd * kKMax;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sl = t >> 7;
-    const int j = (int)(t & (kKMax - 1));
-    const int32_t row = slot_row[sl];
+// padding slots and beyond k / r.  A block (32 x 8 threads) takes 32 slots x 32 columns
+// through shared memory, so both the row-major and the transposed writes are coalesced.
+__global__ void __launch_bounds__(256) k_gather_ud(int64_t ldd, int k, int r, int npad,
+                                                   const int32_t* __restrict__ slot_row,
+                                                   const float* __restrict__ U, int64_t ldu,
+                                                   float* __restrict__ ud_hi, float* __restrict__ ud_lo,
+                                                   float* __restrict__ udt_hi, float* __restrict__ udt_lo) {
+  __shared__ float th[32][33], tl[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t s0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  for (int i = ty; i < 32; i += 8) {  // slot s0 + i, column j0 + tx
+    const int64_t sl = s0 + i;
+    const int j = j0 + tx;
+    const int32_t row = sl < ldd ? slot_row[sl] : -1;
     const float u = (row >= 0 && j < r) ? U[(int64_t)row * ldu + j] : 0.f;
     const float h = tf32_round(u), l = u - h;
-    ud_hi[t] = j < k ? h : 0.f;
-    ud_lo[t] = j < k ? l : 0.f;
-    if (j < npad) {
-      udt_hi[(int64_t)j * ldd + sl] = h;
-      udt_lo[(int64_t)j * ldd + sl] = l;
+    th[i][tx] = h;
+    tl[i][tx] = l;
+    if (sl < ldd) {
+      ud_hi[sl * kKMax + j] = j < k ? h : 0.f;
+      ud_lo[sl * kKMax + j] = j < k ? l : 0.f;
+    }
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {  // column j0 + i, slot s0 + tx
+    const int j = j0 + i;
+    const int64_t sl = s0 + tx;
+    if (j < npad && sl < ldd) {
+      udt_hi[(int64_t)j * ldd + sl] = th[tx][i];
+      udt_lo[(int64_t)j * ldd + sl] = tl[tx][i];
     }
   }
 }
@@ -194,12 +209,15 @@ constexpr int kUpdA = kUpdStages * 2 * kChunkBytes;     // ring of W chunks, hi 
 constexpr int kUpdBytes = kUpdB + kUpdA + 256 + 1024;   // + barriers, 1024-byte alignment slack
 constexpr uint32_t kUpdTmemCols = 256;                  // two 128-column accumulators
 
-// CTA (pt, g): the slot tile pt (N = 128 slots of the core) with its U_D tile resident in
-// shared memory, and the q tiles g, g + G, ... of W streamed by TMA.  Warp 0 loads, warp 1
-// issues the MMAs into one of two tensor-memory accumulators, warps 4-7 apply the update
-// from the other (thread = one q, a row of the core panel).
+// CTA (pt, g): the slot tile pt (128 slots of the core) with its U_D tile resident in shared
+// memory, and the q tiles g, g + G, ... of W streamed by TMA.  The MMA computes X[slot, q]
+// (M = 128 slots, N = 128 q, K = k), so a tensor-memory lane is a slot and the 32 lanes of
+// a warp read and write 32 consecutive slots of one panel row q: 128 contiguous bytes.
+// Warp 0 loads, warp 1 issues the MMAs into one of two accumulators, warps 4-11 apply the
+// update from the other (warp 4 + 4h + i: lanes 32i .. 32i + 31, q columns 64h .. 64h + 63).
+constexpr int kUpdThreads = 384;
 template <int NK>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kUpdThreads, 1)
 k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensorMap mWhi,
               const __grid_constant__ CUtensorMap mWlo, const __grid_constant__ CUtensorMap mUhi,
               const __grid_constant__ CUtensorMap mUlo, const float* __restrict__ A,
@@ -208,8 +226,8 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sB = smem;
-  unsigned char* sA = smem + kUpdB;
+  unsigned char* sB = smem;            // U_D tile: hi chunks 0..3, lo chunks 4..7
+  unsigned char* sA = smem + kUpdB;    // ring of W chunks (hi, lo)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kUpdB + kUpdA);
   uint64_t* barB = bar;
   uint64_t* barFull = bar + 1;                       // [S]
@@ -219,7 +237,7 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
   uint64_t* barDrain = barAccEmpty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barDrain + 1);
   __shared__ int s_abort;
-  __shared__ double s_sum[4][3];
+  __shared__ double s_sum[8][3];
   volatile int* abort_flag = &s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int pt = blockIdx.x % nptiles, g = blockIdx.x / nptiles;
@@ -230,7 +248,7 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
     s_abort = 0;
     mbar_init(barB, 1);
     for (int s = 0; s < kUpdStages; ++s) { mbar_init(barFull + s, 1); mbar_init(barEmpty + s, 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(barAccFull + b, 1); mbar_init(barAccEmpty + b, 128); }
+    for (int b = 0; b < 2; ++b) { mbar_init(barAccFull + b, 1); mbar_init(barAccEmpty + b, 256); }
     mbar_init(barDrain, 1);
     mbar_init_fence();
   }
@@ -262,14 +280,14 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
         tma_load_2d(sA + s * 2 * kChunkBytes + kChunkBytes, &mWlo, c * kKC, tile * kTile, barFull + s);
         issued = j + 1;
       }
-      // after a failure nothing may still land in shared memory when the CTA leaves
+      // nothing may still land in shared memory when the CTA leaves
       mbar_wait(barB, 0);
       if (*abort_flag)
         for (int j = issued - kUpdStages > 0 ? issued - kUpdStages : 0; j < issued; ++j)
           mbar_wait(barFull + j % kUpdStages, (uint32_t)((j / kUpdStages) & 1));
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer
+    if (lane == 0) {  // MMA issuer: A = U_D (slots), B = W (q)
       const uint32_t idesc = instr_desc_tf32(kTile, kTile);
       if (!mbar_wait(barB, 0)) *abort_flag = 1;
       int j = 0;
@@ -282,71 +300,63 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
           const int s = j % kUpdStages;
           if (!mbar_wait(barFull + s, (uint32_t)((j / kUpdStages) & 1))) { *abort_flag = 1; break; }
           fence_after_sync();
-          const unsigned char* a_hi = sA + s * 2 * kChunkBytes;
-          const unsigned char* a_lo = a_hi + kChunkBytes;
-          const unsigned char* b_hi = sB + c * kChunkBytes;
-          const unsigned char* b_lo = sB + (4 + c) * kChunkBytes;
+          const unsigned char* w_hi = sA + s * 2 * kChunkBytes;
+          const unsigned char* w_lo = w_hi + kChunkBytes;
+          const unsigned char* u_hi = sB + c * kChunkBytes;
+          const unsigned char* u_lo = sB + (4 + c) * kChunkBytes;
 #pragma unroll
           for (int kk = 0; kk < kKC / 8; ++kk) {
-            const uint64_t ah = smem_desc(a_hi + kk * 32), al = smem_desc(a_lo + kk * 32);
-            const uint64_t bh = smem_desc(b_hi + kk * 32), bl = smem_desc(b_lo + kk * 32);
-            mma_tf32(acc, ah, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-            mma_tf32(acc, ah, bl, idesc, 1u);
-            mma_tf32(acc, al, bh, idesc, 1u);
+            const uint64_t uh = smem_desc(u_hi + kk * 32), ul = smem_desc(u_lo + kk * 32);
+            const uint64_t wh = smem_desc(w_hi + kk * 32), wl = smem_desc(w_lo + kk * 32);
+            mma_tf32(acc, uh, wh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(acc, uh, wl, idesc, 1u);
+            mma_tf32(acc, ul, wh, idesc, 1u);
           }
           mma_commit(barEmpty + s);
           if (c == NK - 1) mma_commit(barAccFull + b);
         }
       }
     }
-  } else if (warp >= 4) {  // epilogue: thread = one q of the tile, 128 slots
-    const int qw = warp - 4;
+  } else if (warp >= 4) {  // epilogue: thread = one slot, 64 q columns per warp
+    const int lq = warp & 3, half = (warp - 4) >> 2;
+    const int64_t slot = (int64_t)pt * kTile + lq * 32 + lane;
+    const int32_t ld32 = (int32_t)ldd;  // n * ldd < 2^31 (checked by the plan)
     for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
       const int b = t & 1;
       if (!mbar_wait(barAccFull + b, (uint32_t)((t / 2) & 1))) { *abort_flag = 1; break; }
       fence_after_sync();
-      const int tile = g + t * nqgroups;
-      const int64_t q = (int64_t)tile * kTile + qw * 32 + lane;
-      const bool live = q < n;
-      const float* arow = A + (live ? q : 0) * ldd + (int64_t)pt * kTile;
-      float* yrow = Y + (live ? q : 0) * ldd + (int64_t)pt * kTile;
+      const int64_t q0 = (int64_t)(g + t * nqgroups) * kTile + half * 64;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kTile; c0 += 32) {
-        float4 av[8], yv[8];
-        if (live) {
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        const float* ap = A + (q0 + c0) * ldd + slot;
+        const float* yp = Y + (q0 + c0) * ldd + slot;
+        const int live_n = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - (q0 + c0)));
+        float av[32], yv[32];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            av[u] = __ldcs(reinterpret_cast<const float4*>(arow + c0) + u);
-            yv[u] = __ldcs(reinterpret_cast<const float4*>(yrow + c0) + u);
-          }
+        for (int i = 0; i < 32; ++i) {
+          const bool live = i < live_n;
+          av[i] = live ? __ldcs(ap + i * ld32) : __int_as_float(0x7fffffff);
+          yv[i] = live ? __ldcs(yp + i * ld32) : 0.f;
         }
         float x[32];
         {
           float h0[16], h1[16];
-          const uint32_t taddr = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(b * kTile + c0);
+          const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * kTile + half * 64 + c0);
           tmem_ld16(taddr, h0);
           tmem_ld16(taddr + 16, h1);
 #pragma unroll
           for (int i = 0; i < 16; ++i) { x[i] = h0[i]; x[16 + i] = h1[i]; }
         }
-        if (live) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            float a4[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
-            float y4[4] = {yv[u].x, yv[u].y, yv[u].z, yv[u].w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              if (!isnan(a4[i])) {  // observed: the update of eq. (4)
-                const float d = a4[i] - x[4 * u + i];
-                const float yn = fmaf(delta, d, y4[i]);
-                y4[i] = yn;
-                acc_d2.add_sq(d);
-                acc_abs.add(fabsf(d));
-                acc_y2.add_sq(yn);
-                bad |= !isfinite(yn);
-              }
-            }
-            __stcs(reinterpret_cast<float4*>(yrow + c0) + u, make_float4(y4[0], y4[1], y4[2], y4[3]));
+        for (int i = 0; i < 32; ++i) {
+          if (!isnan(av[i])) {  // observed (and q < n): the update of eq. (4)
+            const float d = av[i] - x[i];
+            const float yn = fmaf(delta, d, yv[i]);
+            acc_d2.add_sq(d);
+            acc_abs.add(fabsf(d));
+            acc_y2.add_sq(yn);
+            bad |= !isfinite(yn);
+            __stcs(const_cast<float*>(yp) + i * ld32, yn);
           }
         }
       }
@@ -361,7 +371,11 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
     if (lane == 0) { s_sum[warp - 4][0] = s0; s_sum[warp - 4][1] = s1; s_sum[warp - 4][2] = s2; }
   }
   __syncthreads();
-  if (tid < 3) part[(int64_t)blockIdx.x * 3 + tid] = s_sum[0][tid] + s_sum[1][tid] + s_sum[2][tid] + s_sum[3][tid];
+  if (tid < 3) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += s_sum[w][tid];
+    part[(int64_t)blockIdx.x * 3 + tid] = t;
+  }
   if (tid == 0 && *abort_flag) atomicOr(status, FLAG_TC_TIMEOUT);
   if (warp == 1) {
     if (lane == 0 && *abort_flag) {
@@ -721,13 +735,16 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
   const int nk = (int)ceil_div(k, kKC);
   const int nptiles = (int)(ldd / kTile);
   const int nq = (int)ceil_div(n, kTile);
-  if (nk > 0) {
-    k_split_w<<<egrid(n * kKMax), 256, 0, s>>>(n, k, W, ldw, C.w_hi, C.w_lo);
+  {
+    SVT_PROF("core_split", 4.0 * (double)(n * k + 2 * n * kKMax + ldd * r + 4 * ldd * kKMax), s);
+    if (nk > 0) {
+      k_split_w<<<egrid(n * kKMax), 256, 0, s>>>(n, k, W, ldw, C.w_hi, C.w_lo);
+      SVT_LAUNCH_CHECK();
+    }
+    k_gather_ud<<<dim3((unsigned)ceil_div(ldd, 32), kKMax / 32), 256, 0, s>>>(ldd, k, r, npad, C.slot_row, U, ldu,
+                                                                           C.ud_hi, C.ud_lo, C.udt_hi, C.udt_lo);
     SVT_LAUNCH_CHECK();
   }
-  k_gather_ud<<<egrid(ldd * kKMax), 256, 0, s>>>(ldd, k, r, npad, C.slot_row, U, ldu, C.ud_hi, C.ud_lo,
-                                                  C.udt_hi, C.udt_lo);
-  SVT_LAUNCH_CHECK();
   CUtensorMap mWh, mWl, mUh, mUl, mY, mTh, mTl;
   const uint64_t rowb = (uint64_t)kKMax * 4;
   if (!encode_2d(&mWh, C.w_hi, kKMax, (uint64_t)n, rowb, kKC, kTile) ||
@@ -748,16 +765,19 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
   }
 #define SVT_UPD(NK)                                                                                  \
   case NK:                                                                                           \
-    k_core_update<NK><<<grid1, kThreads, kUpdBytes, s>>>((int)n, nptiles, nqg, mWh, mWl, mUh, mUl,  \
+    k_core_update<NK><<<grid1, kUpdThreads, kUpdBytes, s>>>((int)n, nptiles, nqg, mWh, mWl, mUh, mUl,  \
                                                          C.A, C.Y, ldd, (float)delta, C.part, flags, \
                                                          tc_status);                                 \
     break
-  switch (nk > 0 ? nk : 1) {
-    SVT_UPD(1); SVT_UPD(2); SVT_UPD(3); SVT_UPD(4);
-    default: return fail(SVT_ERR_UNSUPPORTED, "dense core: k = %d", k);
+  {
+    SVT_PROF("core_x_update", 12.0 * (double)(n * ldd) + 8.0 * (double)n * kKMax, s);
+    switch (nk > 0 ? nk : 1) {
+      SVT_UPD(1); SVT_UPD(2); SVT_UPD(3); SVT_UPD(4);
+      default: return fail(SVT_ERR_UNSUPPORTED, "dense core: k = %d", k);
+    }
+    SVT_LAUNCH_CHECK();
   }
 #undef SVT_UPD
-  SVT_LAUNCH_CHECK();
   // B^T += Y_core U_D
   const int nchunks = (int)(ldd / kKC);
 #define SVT_BT(NP)                                                                                   \
@@ -765,12 +785,15 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
     k_core_bt<NP><<<nq, kThreads, BtLayout<NP>::bytes, s>>>((int)n, nchunks, r, mY, mTh, mTl, bt, ldb, \
                                                             tc_status);                              \
     break
-  switch (npad) {
-    SVT_BT(16); SVT_BT(32); SVT_BT(48); SVT_BT(64); SVT_BT(80); SVT_BT(96); SVT_BT(112); SVT_BT(128);
-    default: return fail(SVT_ERR_UNSUPPORTED, "dense core: r = %d", r);
+  {
+    SVT_PROF("core_bt", 4.0 * (double)(n * ldd) + 8.0 * (double)npad * ldd + 8.0 * (double)n * r, s);
+    switch (npad) {
+      SVT_BT(16); SVT_BT(32); SVT_BT(48); SVT_BT(64); SVT_BT(80); SVT_BT(96); SVT_BT(112); SVT_BT(128);
+      default: return fail(SVT_ERR_UNSUPPORTED, "dense core: r = %d", r);
+    }
+    SVT_LAUNCH_CHECK();
   }
 #undef SVT_BT
-  SVT_LAUNCH_CHECK();
   k_core_finish<<<3, 256, 0, s>>>(grid1, C.part, out3);
   SVT_LAUNCH_CHECK();
   return SVT_OK;

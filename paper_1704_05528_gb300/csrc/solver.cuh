@@ -231,6 +231,14 @@ __global__ void k_export_scaled(int64_t rows, int k, int ld, const T* __restrict
   }
 }
 
+// C = (3 I - G) / 2 (r x r): one Newton-Schulz step towards the orthonormal polar factor,
+// Q C, for a basis whose Gram matrix Q^T Q = G is close to the identity.
+__global__ void k_ns_coeff(int r, const double* __restrict__ G, double* __restrict__ C) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)r * r;
+       t += (int64_t)gridDim.x * blockDim.x)
+    C[t] = (t / r == t % r ? 1.5 : 0.0) - 0.5 * G[t];
+}
+
 __global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ ss,
                             double* __restrict__ v) {
   const double inv = 1.0 / sqrt(ss[0]);
@@ -303,6 +311,9 @@ struct Work {
   bool graph_broken = false;
   // the eigen-phase graph of the next R4SVD call was launched ahead by the caller
   bool graph_inflight = false;
+  // set by the caller: re-orthonormalise the recycled basis at the start of the next
+  // R4SVD call (binary32; see reorth_basis)
+  bool reorth_due = false;
   uint64_t graph_clock = 0;
   EigGraph eg[2];
   // graphs are recorded on a private stream (the caller's may be the legacy default
@@ -399,6 +410,46 @@ svt_status lift_basis(Work<T>& W, const T* Q, int r, T* Unew) {
   return gemm_nn<T, T>(W.P.m, r, r, 1.0, Q, W.ldq, W.Ub, r, 0.0, nullptr, 0, Unew, W.ldq, W.s);
 }
 
+// C (M x r, ldc) = A (M x r, lda) B (r x r binary64, ld r): on the tensor cores in the
+// binary32 path when the shape allows, else the SIMT kernel.
+template <typename T>
+svt_status times_small(Work<T>& W, int64_t M, int r, const T* A, int64_t lda, const double* B, T* C,
+                       int64_t ldc) {
+  if constexpr (sizeof(T) == 4) {
+    if (W.tcb && lift_tc_fits(M, r, r, A, lda, C, ldc))
+      return lift_tc(M, r, r, A, lda, B, r, C, ldc, W.tcb, W.flags + 4, W.s);
+  }
+  return gemm_nn<T, T>(M, r, r, 1.0, A, lda, B, r, 0.0, nullptr, 0, C, ldc, W.s);
+}
+
+// Re-orthonormalisation of a binary32 basis by one Newton-Schulz step: Q <- Q C with
+// C = (3 I - Q^T Q) / 2 (the Gram matrix in binary64 accuracy) and, when Bt is given,
+// B^T <- B^T C, which keeps B^T = Y^T Q.  In exact arithmetic Q is orthonormal and C = I; in
+// binary32 each lift U = Q U_B moves Q^T Q away from the identity a little, while the
+// energy test of R4SVD and the SVD of B = Q^T Y assume it is the identity.  The step takes
+// max |Q^T Q - I| from e to about 1.5 e^2.  Qscr (m x ldq) and W.Wk serve as scratch.
+template <typename T>
+svt_status reorth_basis(Work<T>& W, T* Q, int r, T* Qscr, T* Bt, int64_t ldb) {
+  if (r <= 0) return SVT_OK;
+  const int64_t m = W.P.m, n = W.P.n;
+  const int sv = (int)sizeof(T);
+  cudaStream_t st = W.s;
+  SVT_PROF("reorth", gemm_bytes(m, r, 0, sv, false) + 2 * gemm_bytes(m, r, r, sv, false) +
+                         (Bt ? 2 * gemm_bytes(n, r, r, sv, false) : 0.0), st);
+  SVT_TRY((gemm_tn<T, T>(m, r, r, Q, W.ldq, Q, W.ldq, W.G, r, W.part, st)));
+  k_ns_coeff<<<(int)std::min<int64_t>(ceil_div((int64_t)r * r, 256), 256), 256, 0, st>>>(r, W.G, W.Tsm);
+  SVT_LAUNCH_CHECK();
+  SVT_TRY(times_small<T>(W, m, r, Q, W.ldq, W.Tsm, Qscr, W.ldq));
+  SVT_CUDA(cudaMemcpy2DAsync(Q, W.ldq * sizeof(T), Qscr, W.ldq * sizeof(T), r * sizeof(T), m,
+                             cudaMemcpyDeviceToDevice, st));
+  if (Bt) {
+    SVT_TRY(times_small<T>(W, n, r, Bt, ldb, W.Tsm, W.Wk, W.ldk));
+    SVT_CUDA(cudaMemcpy2DAsync(Bt, ldb * sizeof(T), W.Wk, W.ldk * sizeof(T), r * sizeof(T), n,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  return SVT_OK;
+}
+
 enum class EigFrom {
   kClusters,  // near-diagonal cluster start, checked refinement, second pass, else Jacobi
   kRejected,  // the checked refinement from the cluster start was refused: second pass
@@ -475,7 +526,7 @@ svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram,
   SVT_CUDA(cudaStreamSynchronize(st));
   if (tc_status & (FLAG_TC_TIMEOUT | FLAG_GRID_TIMEOUT))
     return fail(SVT_ERR_CUDA, "a bounded wait ran out (%s)",
-                (tc_status & FLAG_TC_TIMEOUT) ? "tensor-core lift" : "grid Jacobi");
+                (tc_status & FLAG_TC_TIMEOUT) ? "tensor-core kernel" : "grid Jacobi");
   prof_flush();
   if (g_prof_on && !near_diagonal) {  // sweep count of the binary32 Jacobi stage (pseudo-entry)
     int sweeps = 0;
@@ -599,6 +650,10 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
   const int sv = (int)sizeof(T);
   const int64_t z = p->nnz;
   auto eps_of = [&](double nb) { return normY2 > 0.0 ? (normY2 - nb) / normY2 : 0.0; };
+  // binary32: a recycled basis is re-orthonormalised when the caller asks (periodically)
+  if (sizeof(T) == 4 && W.reorth_due && s > 0 && !W.graph_inflight)
+    SVT_TRY(reorth_basis<T>(W, Q, s, Unew, W.bt_ready ? W.Bt : nullptr, W.ldb));
+  W.reorth_due = false;
   // A recycled basis whose B^T the fused update already formed usually needs no new block:
   // run the whole eigen phase as one graph and check that assumption afterwards.
   bool have_normB = false;
@@ -617,7 +672,7 @@ svt_status r4svd_run(Work<T>& W, const T* y_csr, const T* y_csc, T* Q, int s, do
         memcpy(fl, hp + 2 * s, sizeof(fl));
         if (fl[4] & (FLAG_TC_TIMEOUT | FLAG_GRID_TIMEOUT))
           return fail(SVT_ERR_CUDA, "a bounded wait ran out (%s)",
-                      (fl[4] & FLAG_TC_TIMEOUT) ? "tensor-core lift" : "grid Jacobi");
+                      (fl[4] & FLAG_TC_TIMEOUT) ? "tensor-core kernel" : "grid Jacobi");
         o->r = s; o->blocks = 0; o->exhausted = false; o->eps = eps0; o->normB = normB;
         o->sigma.assign(s, 0.0);
         if (fl[1] == 0 && fl[3] == 0) {

@@ -54,3 +54,4 @@ def test_grid_barrier_wait_runs_out_and_the_device_stays_usable(env):
     S = got["S"].cpu().numpy()
     assert np.max(np.abs(S - ref.S)) / ref.S[0] < 1e-9
     torch.cuda.synchronize()
+

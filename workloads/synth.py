@@ -122,7 +122,12 @@ def image_512(seed=2) -> Workload:
 
     A = clip(U diag(s) V^T, 0, 255) + N(0,1) noise, s_k = 255 * k^-1.5, U and V Haar
     orthonormal (QR of a Gaussian matrix with the signs of R's diagonal folded in).
-    tau = 5*sqrt(m*n) = 2560, delta = 1.2/0.5 = 2.4, tol 1e-3.
+    tau = 5*sqrt(m*n) = 2560, tol 1e-3.  The step 1.2/p = 2.4 is capped at 1.9, as for the
+    rating workloads: this iterate is not low rank (the noise fills the spectrum), and
+    with a step of 2 or more the iteration is not contractive; at 2.4 the relative residual
+    swings between 0.5 and 1.8 and stalls at 0.58, and differences at the rounding level
+    grow until two binary64 evaluations in different summation orders part by 4e-3 after
+    500 iterations.  At 1.9 the residual falls steadily (0.017 after 500 iterations).
     """
     rng = np.random.default_rng(seed)
     m = n = 512
@@ -144,7 +149,7 @@ def image_512(seed=2) -> Workload:
     r, c, v, hr, hc, hv = _split_entries(rng, m, n, flat, vals, n_hold_unobserved=10000)
     return Workload(name="image_512x512_p0.5", m=m, n=n, rows=r, cols=c, vals=v,
                     held_rows=hr, held_cols=hc, held_vals=hv,
-                    tau=5.0 * math.sqrt(m * n), delta=1.2 / 0.5, tol=1e-3, maxit=500,
+                    tau=5.0 * math.sqrt(m * n), delta=min(1.2 / 0.5, 1.9), tol=1e-3, maxit=500,
                     seed=seed + 0x5EED)
 
 
