@@ -114,6 +114,38 @@ def test_spmm(svt, torch_mod, prec, tol, width):
     assert _rel(got2.cpu().numpy(), Ys.T @ W2.astype(np.float64)) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed", 2e-6)])
+def test_spmm_narrow_widths_on_skewed_rows(svt, torch_mod, prec, tol):
+    """Widths 1-16 take the entry-segmented kernel: rows of thousands of entries that span
+    many chunks, empty rows and columns, and short rows, in both orders."""
+    rng = np.random.default_rng(77)
+    m, n = 900, 700
+    heavy_r = np.repeat(np.array([3, 450, 899], np.int32), 600)
+    heavy_c = np.concatenate([rng.choice(n, 600, replace=False) for _ in range(3)]).astype(np.int32)
+    flat = rng.choice(m * n, size=20000, replace=False)
+    rows = np.concatenate([heavy_r, (flat // n).astype(np.int32)])
+    cols = np.concatenate([heavy_c, (flat % n).astype(np.int32)])
+    keep = (rows % 7 != 5) & (cols % 11 != 4)            # some empty rows and columns
+    key = rows.astype(np.int64) * n + cols
+    _, first = np.unique(key, return_index=True)          # distinct entries only
+    sel = np.zeros(rows.size, bool)
+    sel[first] = True
+    sel &= keep
+    rows, cols = rows[sel], cols[sel]
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    dt = np.float64 if prec == "fp64" else np.float32
+    y = rng.standard_normal(ref_p.nnz).astype(dt)
+    Ys = OF._sparse(ref_p, y.astype(np.float64))
+    for width in (1, 2, 3, 4, 5, 8, 10, 12, 16):
+        W = rng.standard_normal((n, width)).astype(dt)
+        W2 = rng.standard_normal((m, width)).astype(dt)
+        got = svt.spmm(P, torch_mod.from_numpy(y), torch_mod.from_numpy(W), precision=prec)
+        got2 = svt.spmm(P, torch_mod.from_numpy(y), torch_mod.from_numpy(W2), transpose=True, precision=prec)
+        assert _rel(got.cpu().numpy(), Ys @ W.astype(np.float64)) < tol, width
+        assert _rel(got2.cpu().numpy(), Ys.T @ W2.astype(np.float64)) < tol, width
+
+
 # ---------------------------------------------------------- sampled update
 @pytest.mark.parametrize("k", [0, 1, 10, 37])
 def test_sampled_update(svt, torch_mod, k):
