@@ -9,7 +9,8 @@
 // a few rows: on the 71,567 x 10,681 workload the 1,152 rows with at least n/10 entries
 // hold half of the entries at 37% density.  Those rows form the "dense core", stored as
 // a dense n x ldd panel in column-of-A order (element (q, slot) = entry (row[slot], q)),
-// unobserved positions holding a NaN in A and a zero in Y.  On the core the two products
+// kept tile-major in 128 x 128 blocks, unobserved positions holding a NaN in A and a zero
+// in Y.  On the core the two products
 // are dense GEMMs on tcgen05 (three TF32 products per term, binary32 accuracy):
 //   X^T[q, slot] = sum_j W[q, j] U[row[slot], j]          (k_core_update, M = q, N = slot)
 //       epilogue: where A is observed, d = A - x, Y += delta d, sums of d^2, |d|, Y_new^2
@@ -46,6 +47,15 @@ constexpr int kKC = 32;             // K columns per chunk: 128 bytes of binary3
 constexpr int kChunkBytes = kTile * 128;  // one 128 x 32 binary32 chunk: 16 KB
 constexpr int kThreads = 256;
 constexpr int kKMax = 128;          // k <= 128 (four chunks)
+
+// The core panels are stored tile-major: tile (q / 128, slot / 128) is one contiguous block
+// of 128 x 128 values, element (q % 128, slot % 128) at (q % 128) * 128 + slot % 128, so a
+// CTA working on one tile streams one 64 KB block.
+__host__ __device__ __forceinline__ int64_t panel_off(int64_t q, int64_t slot, int64_t ldd) {
+  const int64_t nptiles = ldd / kTile;
+  return ((q / kTile) * nptiles + slot / kTile) * (int64_t)(kTile * kTile) + (q % kTile) * kTile +
+         slot % kTile;
+}
 constexpr int kCoreMaxRows = 4096;  // largest automatic core
 
 // ------------------------------------------------------------------ set-up kernels
@@ -111,14 +121,14 @@ __global__ void k_compact_rest(int32_t n, const int32_t* __restrict__ col_ptr,
 }
 
 // full_src[e] for each CSR slot e of the full pattern: the rest's CSC slot of the entry, or
-// -(1 + q * ldd + slot) for a core entry.
+// -(1 + panel offset of (q, slot)) for a core entry.
 __global__ void k_full_src_core(int64_t z, const int32_t* __restrict__ csr_row,
                                 const int32_t* __restrict__ col_idx, const int32_t* __restrict__ row_slot,
                                 int64_t ldd, int32_t* __restrict__ full_src) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < z;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t sl = row_slot[csr_row[e]];
-    if (sl >= 0) full_src[e] = -(int32_t)(1 + (int64_t)col_idx[e] * ldd + sl);
+    if (sl >= 0) full_src[e] = -(int32_t)(1 + panel_off(col_idx[e], sl, ldd));
   }
 }
 __global__ void k_full_src_rest(int64_t zr, const int32_t* __restrict__ rest_full,
@@ -128,7 +138,7 @@ __global__ void k_full_src_rest(int64_t zr, const int32_t* __restrict__ rest_ful
     full_src[perm[rest_full[c]]] = (int32_t)c;
 }
 
-// Core panel from a full CSC-order vector: panel[q * ldd + slot] = src_csc[c] for core entries.
+// Core panel from a full CSC-order vector: panel(q, slot) = src_csc[c] for core entries.
 __global__ void k_scatter_core(int64_t z, const int32_t* __restrict__ perm,
                                const int32_t* __restrict__ csr_row, const int32_t* __restrict__ col_idx,
                                const int32_t* __restrict__ row_slot, int64_t ldd,
@@ -137,7 +147,7 @@ __global__ void k_scatter_core(int64_t z, const int32_t* __restrict__ perm,
        c += (int64_t)gridDim.x * blockDim.x) {
     const int32_t e = perm[c];
     const int32_t sl = row_slot[csr_row[e]];
-    if (sl >= 0) panel[(int64_t)col_idx[e] * ldd + sl] = src_csc[c];
+    if (sl >= 0) panel[panel_off(col_idx[e], sl, ldd)] = src_csc[c];
   }
 }
 
@@ -319,24 +329,24 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
     }
   } else if (warp >= 4) {  // epilogue: thread = one slot, 64 q columns per warp
     const int lq = warp & 3, half = (warp - 4) >> 2;
-    const int64_t slot = (int64_t)pt * kTile + lq * 32 + lane;
-    const int32_t ld32 = (int32_t)ldd;  // n * ldd < 2^31 (checked by the plan)
     for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
       const int b = t & 1;
       if (!mbar_wait(barAccFull + b, (uint32_t)((t / 2) & 1))) { *abort_flag = 1; break; }
       fence_after_sync();
       const int64_t q0 = (int64_t)(g + t * nqgroups) * kTile + half * 64;
+      // this tile's 64 KB block of each panel: rows q of 128 slots
+      const int64_t tile_base = ((int64_t)(g + t * nqgroups) * nptiles + pt) * (int64_t)(kTile * kTile);
 #pragma unroll 1
       for (int c0 = 0; c0 < 64; c0 += 32) {
-        const float* ap = A + (q0 + c0) * ldd + slot;
-        const float* yp = Y + (q0 + c0) * ldd + slot;
+        const float* ap = A + tile_base + (int64_t)(half * 64 + c0) * kTile + lq * 32 + lane;
+        const float* yp = Y + tile_base + (int64_t)(half * 64 + c0) * kTile + lq * 32 + lane;
         const int live_n = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - (q0 + c0)));
         float av[32], yv[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const bool live = i < live_n;
-          av[i] = live ? __ldcs(ap + i * ld32) : __int_as_float(0x7fffffff);
-          yv[i] = live ? __ldcs(yp + i * ld32) : 0.f;
+          av[i] = live ? __ldcs(ap + i * kTile) : __int_as_float(0x7fffffff);
+          yv[i] = live ? __ldcs(yp + i * kTile) : 0.f;
         }
         float x[32];
         {
@@ -356,7 +366,7 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
             acc_abs.add(fabsf(d));
             acc_y2.add_sq(yn);
             bad |= !isfinite(yn);
-            __stcs(const_cast<float*>(yp) + i * ld32, yn);
+            __stcs(const_cast<float*>(yp) + i * kTile, yn);
           }
         }
       }
@@ -452,7 +462,7 @@ k_core_bt(int n, int nchunks, int r, const __grid_constant__ CUtensorMap mY,
         }
         unsigned char* st = stage(s);
         mbar_expect_tx(barFull + s, (uint32_t)(kChunkBytes + 2 * L::kBChunk));
-        tma_load_2d(st, &mY, c * kKC, tile * kTile, barFull + s);
+        tma_load_4d(st, &mY, (c % (kTile / kKC)) * kKC, 0, c / (kTile / kKC), tile, barFull + s);
         tma_load_2d(st + 2 * kChunkBytes, &mUthi, c * kKC, 0, barFull + s);
         tma_load_2d(st + 2 * kChunkBytes + L::kBChunk, &mUtlo, c * kKC, 0, barFull + s);
         issued = c + 1;
@@ -546,6 +556,21 @@ k_core_finish(int nparts, const double* __restrict__ part, double* __restrict__ 
   if (threadIdx.x == 0) out3[c] += s;
 }
 
+// The tile-major Y panel as a 4-D tensor (slot in tile, q in tile, slot tile, q tile) whose
+// box (32 slots, 128 q, 1, 1) is one K chunk of a q tile: the layout of a 2-D box of 32 x 128.
+bool encode_panel_4d(CUtensorMap* map, const float* base, int64_t nptiles, int64_t nqt) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t gdim[4] = {(cuuint64_t)kTile, (cuuint64_t)kTile, (cuuint64_t)nptiles, (cuuint64_t)nqt};
+  cuuint64_t gstr[3] = {(cuuint64_t)kTile * 4, (cuuint64_t)kTile * kTile * 4,
+                        (cuuint64_t)nptiles * kTile * kTile * 4};
+  cuuint32_t box[4] = {(cuuint32_t)kKC, (cuuint32_t)kTile, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int egrid(int64_t work) {
   const int64_t g = ceil_div(work > 0 ? work : 1, 256);
   const int64_t cap = (int64_t)num_sms() * 8;
@@ -605,7 +630,7 @@ svt_status core_plan(const svt_pattern* p, int want_rows, double min_frac, cudaS
   }
   if (rd <= 0) return SVT_OK;
   const int64_t ldd = round_up(rd, kTile);
-  if (n * ldd >= (int64_t)INT32_MAX - 1) return SVT_OK;  // panel offsets must fit int32
+  if (round_up(n, kTile) * ldd >= (int64_t)INT32_MAX - 1) return SVT_OK;  // panel offsets fit int32
   std::vector<int32_t> rows(order.begin(), order.begin() + rd);
   std::sort(rows.begin(), rows.end());
   plan->rd = (int)rd;
@@ -636,7 +661,7 @@ CorePlan core_plan_bound(int64_t m, int64_t n, int64_t nnz, int want_rows, doubl
   }
   if (rd <= 0) return b;
   const int64_t ldd = round_up(rd, kTile);
-  if (n * ldd >= (int64_t)INT32_MAX - 1) return b;
+  if (round_up(n, kTile) * ldd >= (int64_t)INT32_MAX - 1) return b;
   b.rd = (int)rd;
   b.ldd = ldd;
   b.core_nnz = 0;
@@ -658,8 +683,8 @@ void core_layout(Arena& a, const CorePlan& plan, int64_t m, int64_t n, int r_cap
   C->rest_chunk_col = a.take<int32_t>(C->rest.nchunks);
   C->a_rest = a.take<float>(zr);
   C->y_rest = a.take<float>(zr);
-  C->A = a.take<float>(n * ldd);
-  C->Y = a.take<float>(n * ldd);
+  C->A = a.take<float>(round_up(n, kTile) * ldd);
+  C->Y = a.take<float>(round_up(n, kTile) * ldd);
   C->w_hi = a.take<float>(n * kKMax);
   C->w_lo = a.take<float>(n * kKMax);
   C->ud_hi = a.take<float>(ldd * kKMax);
@@ -700,7 +725,7 @@ svt_status core_build(const svt_pattern* p, const CorePlan& plan, const float* a
     SVT_TRY(launch_gather<float>(zr, C->rest_full, a_csc, C->a_rest, s));
   }
   // observed values on the core panel, NaN (all bits set) where nothing is observed
-  SVT_CUDA(cudaMemsetAsync(C->A, 0xFF, n * ldd * sizeof(float), s));
+  SVT_CUDA(cudaMemsetAsync(C->A, 0xFF, round_up(n, kTile) * ldd * sizeof(float), s));
   k_scatter_core<<<egrid(z), 256, 0, s>>>(z, p->perm, p->csr_row, p->col_idx, C->row_slot, ldd, a_csc, C->A);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
@@ -709,7 +734,7 @@ svt_status core_build(const svt_pattern* p, const CorePlan& plan, const float* a
 svt_status core_enter(const svt_pattern* p, const float* y_csc, cudaStream_t s, DenseCore* C) {
   const int64_t z = p->nnz, zr = C->rest.nnz;
   if (zr > 0) SVT_TRY(launch_gather<float>(zr, C->rest_full, y_csc, C->y_rest, s));
-  SVT_CUDA(cudaMemsetAsync(C->Y, 0, C->n * C->ldd * sizeof(float), s));
+  SVT_CUDA(cudaMemsetAsync(C->Y, 0, round_up(C->n, kTile) * C->ldd * sizeof(float), s));
   k_scatter_core<<<egrid(z), 256, 0, s>>>(z, p->perm, p->csr_row, p->col_idx, C->row_slot, C->ldd, y_csc, C->Y);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
@@ -751,7 +776,7 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
       !encode_2d(&mWl, C.w_lo, kKMax, (uint64_t)n, rowb, kKC, kTile) ||
       !encode_2d(&mUh, C.ud_hi, kKMax, (uint64_t)ldd, rowb, kKC, kTile) ||
       !encode_2d(&mUl, C.ud_lo, kKMax, (uint64_t)ldd, rowb, kKC, kTile) ||
-      !encode_2d(&mY, C.Y, (uint64_t)ldd, (uint64_t)n, (uint64_t)ldd * 4, kKC, kTile) ||
+      !encode_panel_4d(&mY, C.Y, ldd / kTile, ceil_div(n, kTile)) ||
       !encode_2d(&mTh, C.udt_hi, (uint64_t)ldd, (uint64_t)npad, (uint64_t)ldd * 4, kKC, (uint32_t)npad) ||
       !encode_2d(&mTl, C.udt_lo, (uint64_t)ldd, (uint64_t)npad, (uint64_t)ldd * 4, kKC, (uint32_t)npad))
     return fail(SVT_ERR_CUDA, "dense core: tensor map encoding failed");

@@ -54,6 +54,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
       : "memory");
 }
+// 4-D tiled load, coordinates innermost first.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            int w, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
+          saddr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(saddr(bar))
+      : "memory");
+}
 // Shared-memory matrix descriptor of a K-major operand with 128-byte swizzle: rows of 128
 // bytes, groups of eight rows 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
