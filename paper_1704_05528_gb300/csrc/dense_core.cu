@@ -329,8 +329,16 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
     }
   } else if (warp >= 4) {  // epilogue: thread = one slot, 64 q columns per warp
     const int lq = warp & 3, half = (warp - 4) >> 2;
+    // the panel blocks of A and Y a tile reads (64 KB each), fetched into L2 one tile ahead
+    auto prefetch_tile = [&](int t) {
+      const int64_t base = ((int64_t)(g + t * nqgroups) * nptiles + pt) * (int64_t)(kTile * kTile);
+      prefetch_l2(A + base, kTile * kTile * 4);
+      prefetch_l2(Y + base, kTile * kTile * 4);
+    };
+    if (tid == 128 && my_tiles > 0) prefetch_tile(0);
     for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
       const int b = t & 1;
+      if (tid == 128 && t + 1 < my_tiles) prefetch_tile(t + 1);
       if (!mbar_wait(barAccFull + b, (uint32_t)((t / 2) & 1))) { *abort_flag = 1; break; }
       fence_after_sync();
       const int64_t q0 = (int64_t)(g + t * nqgroups) * kTile + half * 64;
@@ -400,6 +408,7 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
 
 // ------------------------------------------------------------------ B^T += Y_core U_D
 constexpr int kBtStages = 3;
+constexpr int kBtSplitters = 192;  // warps 2-7 split the chunks of Y
 
 template <int NPAD>
 struct BtLayout {
@@ -410,14 +419,15 @@ struct BtLayout {
 };
 
 // One CTA per q tile: B^T[q tile, :r] += Y[q tile, :] U_D, with K = ldd slots in chunks of
-// 32.  Warp 0 loads a chunk of Y and of U_D^T (high and low parts), warps 2-3 split the
-// chunk of Y in place into its TF32 parts, warp 1 issues the MMAs, warps 4-7 add the
-// accumulator to the rows of B^T.
+// 32.  Warp 0 loads a chunk of Y and of U_D^T (high and low parts), warps 2-7 split the
+// chunk of Y in place into its TF32 parts, warp 1 issues the MMAs, and at the end warps
+// 4-7 add the accumulator to the rows of B^T.
 template <int NPAD>
 __global__ void __launch_bounds__(kThreads, 1)
 k_core_bt(int n, int nchunks, int r, const __grid_constant__ CUtensorMap mY,
           const __grid_constant__ CUtensorMap mUthi, const __grid_constant__ CUtensorMap mUtlo,
-          float* __restrict__ bt, int64_t ldb, unsigned* __restrict__ status) {
+          const float* __restrict__ Ypanel, float* __restrict__ bt, int64_t ldb,
+          unsigned* __restrict__ status) {
   using L = BtLayout<NPAD>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -437,7 +447,7 @@ k_core_bt(int n, int nchunks, int r, const __grid_constant__ CUtensorMap mY,
     s_abort = 0;
     for (int s = 0; s < kBtStages; ++s) {
       mbar_init(barFull + s, 1);
-      mbar_init(barSplit + s, 64);
+      mbar_init(barSplit + s, kBtSplitters);
       mbar_init(barEmpty + s, 1);
     }
     mbar_init(barAcc, 1);
@@ -453,9 +463,17 @@ k_core_bt(int n, int nchunks, int r, const __grid_constant__ CUtensorMap mY,
 
   if (warp == 0) {
     if (lane == 0) {
+      // this q tile's panel blocks (64 KB each, one per 128 slots), fetched into L2 one
+      // block ahead of the chunk loads
+      const int nptiles = nchunks / (kTile / kKC);
+      const float* yblk = Ypanel + (int64_t)tile * nptiles * (kTile * kTile);
+      prefetch_l2(yblk, kTile * kTile * 4);
       int issued = 0;
       for (int c = 0; c < nchunks && !*abort_flag; ++c) {
         const int s = c % kBtStages;
+        const int pb = c / (kTile / kKC) + 1;
+        if (c % (kTile / kKC) == 0 && pb < nptiles)
+          prefetch_l2(yblk + (int64_t)pb * (kTile * kTile), kTile * kTile * 4);
         if (c >= kBtStages && !mbar_wait(barEmpty + s, (uint32_t)((c / kBtStages - 1) & 1))) {
           *abort_flag = 1;
           break;
@@ -470,24 +488,6 @@ k_core_bt(int n, int nchunks, int r, const __grid_constant__ CUtensorMap mY,
       if (*abort_flag)
         for (int c = issued - kBtStages > 0 ? issued - kBtStages : 0; c < issued; ++c)
           mbar_wait(barFull + c % kBtStages, (uint32_t)((c / kBtStages) & 1));
-    }
-  } else if (warp == 2 || warp == 3) {  // split the chunk of Y: 64 threads
-    const int t64 = tid - 64;
-    for (int c = 0; c < nchunks && !*abort_flag; ++c) {
-      const int s = c % kBtStages;
-      if (!mbar_wait(barFull + s, (uint32_t)((c / kBtStages) & 1))) { *abort_flag = 1; break; }
-      float4* hi4 = reinterpret_cast<float4*>(stage(s));
-      float4* lo4 = reinterpret_cast<float4*>(stage(s) + kChunkBytes);
-#pragma unroll 4
-      for (int i = t64; i < kChunkBytes / 16; i += 64) {
-        const float4 x = hi4[i];
-        float4 h;
-        h.x = tf32_round(x.x); h.y = tf32_round(x.y); h.z = tf32_round(x.z); h.w = tf32_round(x.w);
-        hi4[i] = h;
-        lo4[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      }
-      fence_proxy_async();
-      mbar_arrive(barSplit + s);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -512,20 +512,65 @@ k_core_bt(int n, int nchunks, int r, const __grid_constant__ CUtensorMap mY,
         if (c == nchunks - 1) mma_commit(barAcc);
       }
     }
-  } else {  // warps 4-7: B^T rows += accumulator
-    const int qw = warp - 4;
-    if (!*abort_flag && mbar_wait(barAcc, 0)) {
+  } else {  // warps 2-7 split the chunks of Y; then warps 4-7 add the accumulator to B^T
+    const int ts = tid - 64;
+    for (int c = 0; c < nchunks && !*abort_flag; ++c) {
+      const int s = c % kBtStages;
+      if (!mbar_wait(barFull + s, (uint32_t)((c / kBtStages) & 1))) { *abort_flag = 1; break; }
+      float4* hi4 = reinterpret_cast<float4*>(stage(s));
+      float4* lo4 = reinterpret_cast<float4*>(stage(s) + kChunkBytes);
+#pragma unroll 2
+      for (int i = ts; i < kChunkBytes / 16; i += kBtSplitters) {
+        const float4 x = hi4[i];
+        float4 h;
+        h.x = tf32_round(x.x); h.y = tf32_round(x.y); h.z = tf32_round(x.z); h.w = tf32_round(x.w);
+        hi4[i] = h;
+        lo4[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      fence_proxy_async();
+      mbar_arrive(barSplit + s);
+    }
+    if (warp < 4) {
+      // warps 2-3 are done
+    } else if (!*abort_flag && mbar_wait(barAcc, 0)) {
+      // Accumulator rows -> a shared tile (the stages are idle once the last MMA has
+      // completed) -> whole rows of B^T, read, added to and written back coalesced.  Warp
+      // qw owns tile rows 32 qw .. 32 qw + 31 in both steps.
+      const int qw = warp - 4;
       fence_after_sync();
-      const int64_t q = (int64_t)tile * kTile + qw * 32 + lane;
+      float* tileT = reinterpret_cast<float*>(smem);
+      constexpr int kLd = NPAD + 1;  // odd: the 32 rows of a column fall in 32 banks
+      static_assert(kTile * kLd * 4 <= kBtStages * L::kStage, "B^T staging tile");
+      const int ql = qw * 32 + lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < NPAD; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)c0, v);
-        if (q < n) {
-          float* dst = bt + q * ldb + c0;
 #pragma unroll
-          for (int u = 0; u < 16; ++u)
-            if (c0 + u < r) dst[u] += v[u];
+        for (int u = 0; u < 16; ++u) tileT[ql * kLd + c0 + u] = v[u];
+      }
+      __syncwarp();
+      constexpr int kCols = (NPAD + 31) / 32;
+#pragma unroll 1
+      for (int i0 = 0; i0 < 32; i0 += 8) {
+        float cur[8][kCols];
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const int64_t q = (int64_t)tile * kTile + qw * 32 + i0 + ii;
+#pragma unroll
+          for (int c = 0; c < kCols; ++c) {
+            const int j = c * 32 + lane;
+            cur[ii][c] = (q < n && j < r) ? bt[q * ldb + j] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const int64_t q = (int64_t)tile * kTile + qw * 32 + i0 + ii;
+#pragma unroll
+          for (int c = 0; c < kCols; ++c) {
+            const int j = c * 32 + lane;
+            if (q < n && j < r) bt[q * ldb + j] = cur[ii][c] + tileT[(qw * 32 + i0 + ii) * kLd + j];
+          }
         }
       }
     } else {
@@ -807,7 +852,7 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
   const int nchunks = (int)(ldd / kKC);
 #define SVT_BT(NP)                                                                                   \
   case NP:                                                                                           \
-    k_core_bt<NP><<<nq, kThreads, BtLayout<NP>::bytes, s>>>((int)n, nchunks, r, mY, mTh, mTl, bt, ldb, \
+    k_core_bt<NP><<<nq, kThreads, BtLayout<NP>::bytes, s>>>((int)n, nchunks, r, mY, mTh, mTl, C.Y, bt, ldb, \
                                                             tc_status);                              \
     break
   {

@@ -11,8 +11,10 @@
 //     symmetric eigenvalue decomposition", 2018): with X the current eigenvector
 //     estimate, R = I - X^T X, S = X^T G X, lam_i = S_ii / (1 - R_ii), and
 //     E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) for well separated pairs,
-//     E_ij = R_ij / 2 otherwise; X <- X + X E.  Each step is four r x r x r products
-//     (spread over the whole GPU) and converges quadratically.  A pair counts as well
+//     E_ij = R_ij / 2 otherwise; X <- X + X E.  P = G X is formed once and then carried
+//     through the updates (G (X + X E) = P + P E), so a step is three launches: E, the
+//     update of [X | P] and X^T [X | P] (r x r x r products spread over the whole GPU);
+//     it converges quadratically.  A pair counts as well
 //     separated when its first-order correction is below 0.1 (a per-pair test: the
 //     paper's global bound built from Frobenius norms lumps a dense spectrum together).
 // The eigenpairs are finally sorted by descending eigenvalue.
@@ -243,70 +245,94 @@ __global__ void k_to_double_ld(int r, const float* __restrict__ src, double* __r
 // (= S_ii / (1 - R_ii)), and E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i) wherever that
 // first-order correction is small (|E_ij| < 0.1); pairs too close for it to be
 // trustworthy are left as a cluster with E_ij = R_ij / 2, as are the diagonal entries.
-__global__ void k_oa_lambda(int r, const double* __restrict__ CS, double* __restrict__ lam) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// CS = [C | S] is r x 2r (leading dimension 2r).
+__device__ __forceinline__ double oa_coeff(int r, const double* __restrict__ CS, int a, int b) {
   const int64_t ld = 2 * (int64_t)r;
-  if (i < r) lam[i] = CS[i * ld + r + i] / CS[i * ld + i];
+  const double cab = CS[a * ld + b], sab = CS[a * ld + r + b];
+  const double rab = (a == b ? 1.0 : 0.0) - cab;
+  double e = 0.5 * rab;
+  if (a != b) {
+    const double la = CS[a * ld + r + a] / CS[a * ld + a];
+    const double lb = CS[b * ld + r + b] / CS[b * ld + b];
+    const double gap = lb - la;
+    if (gap != 0.0) {
+      const double f = (sab + lb * rab) / gap;
+      if (fabs(f) < 0.1) e = f;
+    }
+  }
+  return e;
 }
 
 __global__ void k_oa_coeffs(int r, const double* __restrict__ CS, double* __restrict__ E) {
-  const int64_t ld = 2 * (int64_t)r;
   const int rr2 = r * r;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rr2; t += gridDim.x * blockDim.x) {
-    const int a = t / r, b = t - (t / r) * r;
-    const double cab = CS[a * ld + b], sab = CS[a * ld + r + b];
-    const double rab = (a == b ? 1.0 : 0.0) - cab;
-    double e = 0.5 * rab;
-    if (a != b) {
-      const double la = CS[a * ld + r + a] / CS[a * ld + a];
-      const double lb = CS[b * ld + r + b] / CS[b * ld + b];
-      const double gap = lb - la;
-      if (gap != 0.0) {
-        const double f = (sab + lb * rab) / gap;
-        if (fabs(f) < 0.1) e = f;
-      }
-    }
-    E[t] = e;
-  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rr2; t += gridDim.x * blockDim.x)
+    E[t] = oa_coeff(r, CS, t / r, t - (t / r) * r);
 }
 
-// Convergence test of the refinement: *status = 1 when an off-diagonal entry of
-// S = X^T G X exceeds tol times its largest diagonal entry (a coupled pair was left
-// unresolved), else 0.
+// [X | P] <- [X | P] + [X | P] E, blockwise (X E and P E).  P = G X is carried through the
+// update instead of being formed again from G: G (X + X E) = P + P E.  XP and XPn are
+// r x 2r (leading dimension l2); blockIdx.z selects the X or the P block.  Each output is
+// sum_l A[i][l] E[l][j] in the order of l, then + A[i][j].
+__global__ void __launch_bounds__(kSgTile * kSgTile)
+k_oa_update(int r, const double* __restrict__ XP, int64_t l2, const double* __restrict__ E,
+            double* __restrict__ XPn) {
+  constexpr int T = kSgTile;
+  __shared__ double As[T][T + 1];
+  __shared__ double Es[T][T + 1];
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  const int i = blockIdx.y * T + ty, j = blockIdx.x * T + tx;
+  const double* Ab = XP + (int64_t)blockIdx.z * r;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < r; k0 += T) {
+    const int ka = k0 + tx, kb = k0 + ty;
+    As[ty][tx] = (i < r && ka < r) ? Ab[(int64_t)i * l2 + ka] : 0.0;
+    Es[ty][tx] = (kb < r && j < r) ? E[(int64_t)kb * r + j] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < T; ++kk) acc = fma(As[ty][kk], Es[kk][tx], acc);
+    __syncthreads();
+  }
+  if (i < r && j < r) XPn[(int64_t)i * l2 + (int64_t)blockIdx.z * r + j] = acc + Ab[(int64_t)i * l2 + j];
+}
+
+// The end of a refinement, in one block of 1024 threads (r <= 1024): the eigenvalues
+// lam_i = S_ii / C_ii; when `status` is given, the convergence test (*status = 1 when an
+// off-diagonal entry of S = X^T G X exceeds tol times its largest diagonal entry, i.e. a
+// coupled pair was left unresolved, else 0); then the eigenpairs sorted by descending
+// eigenvalue (bitonic network over the next power of two >= r, ties by index) into
+// lam_out and the columns of Ub.
 __global__ void __launch_bounds__(1024)
-k_oa_check(int r, const double* __restrict__ CS, double tol, int* __restrict__ status) {
+k_oa_finish(int r, const double* __restrict__ CS, double tol, int* __restrict__ status,
+            const double* __restrict__ X, int64_t ldx, double* __restrict__ lam_out,
+            double* __restrict__ Ub, int64_t ldu) {
+  __shared__ double key[1024];
+  __shared__ int idx[1024];
   __shared__ double red_off[32], red_diag[32];
+  const int t = threadIdx.x;
   const int64_t ld = 2 * (int64_t)r;
-  double off = 0.0, dg = 0.0;
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-    const int a = t / r, b = t - (t / r) * r;
-    const double v = fabs(CS[a * ld + r + b]);
-    if (a == b) dg = fmax(dg, v); else off = fmax(off, v);
+  if (status) {
+    double off = 0.0, dg = 0.0;
+    for (int e = t; e < r * r; e += blockDim.x) {
+      const int a = e / r, b = e - (e / r) * r;
+      const double v = fabs(CS[a * ld + r + b]);
+      if (a == b) dg = fmax(dg, v); else off = fmax(off, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
+      dg = fmax(dg, __shfl_xor_sync(0xffffffffu, dg, o));
+    }
+    if ((t & 31) == 0) { red_off[t >> 5] = off; red_diag[t >> 5] = dg; }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
-    dg = fmax(dg, __shfl_xor_sync(0xffffffffu, dg, o));
-  }
-  if ((threadIdx.x & 31) == 0) { red_off[threadIdx.x >> 5] = off; red_diag[threadIdx.x >> 5] = dg; }
+  int P = 2;
+  while (P < r) P <<= 1;
+  key[t] = t < r ? CS[t * ld + r + t] / CS[t * ld + t] : -INFINITY;
+  idx[t] = t;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (status && t == 0) {
+    double off = red_off[0], dg = red_diag[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { off = fmax(off, red_off[w]); dg = fmax(dg, red_diag[w]); }
     *status = (off <= tol * dg) ? 0 : 1;  // NaN counts as not converged
   }
-}
-
-// Sort eigenpairs by descending eigenvalue (bitonic over 1024 slots, r <= 1024).
-__global__ void __launch_bounds__(1024)
-k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ X, int64_t ldx,
-           double* __restrict__ lam_out, double* __restrict__ Ub, int64_t ldu) {
-  __shared__ double key[1024];
-  __shared__ int idx[1024];
-  const int t = threadIdx.x;
-  int P = 2;  // bitonic network over the next power of two >= r
-  while (P < r) P <<= 1;
-  key[t] = t < r ? lam_in[t] : -INFINITY;
-  idx[t] = t;
-  __syncthreads();
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       const int ixj = t ^ j;
@@ -314,7 +340,6 @@ k_sort_eig(int r, const double* __restrict__ lam_in, const double* __restrict__ 
         const bool desc = (t & k) == 0;
         const double a = key[t], b = key[ixj];
         const int ia = idx[t], ib = idx[ixj];
-        // order: larger first (ties broken by index) when desc
         const bool a_first = (a > b) || (a == b && ia < ib);
         if (desc != a_first) {
           key[t] = b; key[ixj] = a; idx[t] = ib; idx[ixj] = ia;
@@ -807,25 +832,21 @@ svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* 
     return SVT_OK;
   };
   const int steps = refine_steps > 0 ? refine_steps : 0;
-  const int eb = (int)ceil_div((int64_t)r * r, 256);
   double* XP = w.XP;
   double* XPn = w.XPn;
-  for (int step = 0; step <= steps; ++step) {
-    SVT_TRY(gemm(false, r, r, r, G, ldg, XP, l2, 0.0, nullptr, 0, XP + r, l2));    // P = G X
-    SVT_TRY(gemm(true, r, 2 * r, r, XP, l2, XP, l2, 0.0, nullptr, 0, w.CS, l2));  // X^T [X | P]
-    if (step == steps) break;                                                     // eigenvalues only
+  SVT_TRY(gemm(false, r, r, r, G, ldg, XP, l2, 0.0, nullptr, 0, XP + r, l2));  // P = G X
+  SVT_TRY(gemm(true, r, 2 * r, r, XP, l2, XP, l2, 0.0, nullptr, 0, w.CS, l2));  // X^T [X | P]
+  const dim3 ugrid((unsigned)ceil_div(r, kSgTile), (unsigned)ceil_div(r, kSgTile), 2);
+  const int eb = (int)ceil_div((int64_t)r * r, 256);
+  for (int step = 0; step < steps; ++step) {
     k_oa_coeffs<<<eb < 1024 ? eb : 1024, 256, 0, s>>>(r, w.CS, w.E);
     SVT_LAUNCH_CHECK();
-    SVT_TRY(gemm(false, r, r, r, XP, l2, w.E, r, 1.0, XP, l2, XPn, l2));           // X + X E
-    double* t = XP; XP = XPn; XPn = t;
-  }
-  k_oa_lambda<<<(int)ceil_div(r, 256), 256, 0, s>>>(r, w.CS, w.lam);
-  SVT_LAUNCH_CHECK();
-  if (check_status) {
-    k_oa_check<<<1, 1024, 0, s>>>(r, w.CS, check_tol, check_status);
+    k_oa_update<<<ugrid, kSgTile * kSgTile, 0, s>>>(r, XP, l2, w.E, XPn);       // [X | P] (I + E)
     SVT_LAUNCH_CHECK();
+    double* t = XP; XP = XPn; XPn = t;
+    SVT_TRY(gemm(true, r, 2 * r, r, XP, l2, XP, l2, 0.0, nullptr, 0, w.CS, l2));  // X^T [X | P]
   }
-  k_sort_eig<<<1, 1024, 0, s>>>(r, w.lam, XP, l2, lam, Ub, ldu);
+  k_oa_finish<<<1, 1024, 0, s>>>(r, w.CS, check_tol, check_status, XP, l2, lam, Ub, ldu);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }

@@ -63,6 +63,10 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(saddr(bar))
       : "memory");
 }
+// Asynchronous prefetch of `bytes` (a multiple of 16, 16-byte aligned start) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 // Shared-memory matrix descriptor of a K-major operand with 128-byte swizzle: rows of 128
 // bytes, groups of eight rows 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
