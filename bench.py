@@ -527,6 +527,8 @@ def our_arm(args):
     core_parts = {k: prof.pop(k) for k in list(prof) if k.startswith("core_")}
     events = {k: prof.pop(k)["launches"] for k in ("eig_start_oversize", "eig_start_rejected",
                                                    "eig_start_rejected_twice",
+                                                   "eig_jacobi_more_steps", "eig_jacobi_clusters",
+                                                   "eig_jacobi_unresolved",
                                                    "eig_graph_unavailable") if k in prof}
     classes = dict(prof)
     if "update_core" in classes:  # one step: rest + core, per launch of the pair

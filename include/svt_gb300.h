@@ -189,8 +189,8 @@ svt_status svt_spmm(const svt_pattern* p, int precision, int transpose, const vo
  * its contents persist from call to call; nothing in it needs to start at zero, but
  * calls that overlap on the GPU race on it.  The first call on a device looks up the
  * array's address there and caches it for the process, so a device reset
- * (cudaDeviceReset) while the library is in use is not supported.  The call waits for
- * its stream before returning, so it cannot be recorded into a stream capture.
+ * (cudaDeviceReset) while the library is in use is not supported; make that first call
+ * before any stream capture.
  * y_csr must hold the pattern's nnz values and W its n (transpose = 0) or m
  * (transpose = 1) rows: the library cannot check buffer sizes. */
 svt_status svt_spmm_noalloc(const svt_pattern* p, int precision, int transpose,

@@ -381,8 +381,7 @@ svt_status rayleigh_ritz(Work<T>& W, const svt_pattern* pl, const T* y_csc, cons
   SVT_TRY((launch_spmm_rows<T, T>(n, pl->col_ptr, pl->row_idx, y_csc, Q, W.ldq, r, W.Bt, W.ldb,
                                    W.spmm_scr, pl->nnz, st, pl->chunk_row_csc)));
   SVT_TRY((gemm_tn<T, T>(n, r, r, W.Bt, W.ldb, W.Bt, W.ldb, W.G, r, W.part, st)));
-  SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2), W.flags + 4));
-  SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
+  SVT_TRY(eig_from_jacobi<T>(W, r));
   SVT_TRY(lift_basis<T>(W, Q, r, U));
   std::vector<double> lam(r);
   SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));

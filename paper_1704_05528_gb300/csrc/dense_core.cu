@@ -336,50 +336,65 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
       prefetch_l2(Y + base, kTile * kTile * 4);
     };
     if (tid == 128 && my_tiles > 0) prefetch_tile(0);
-    for (int t = 0; t < my_tiles && !*abort_flag; ++t) {
+    // Batches of 16 q rows, four per tile; the loads of the next batch are issued before
+    // the current one is processed, so one batch of A and Y is always in flight.
+    constexpr int kRows = 16;
+    const int nb = my_tiles * (64 / kRows);
+    auto load_batch = [&](int j, float (&av)[kRows], float (&yv)[kRows]) {
+      const int t = j / (64 / kRows), bi = j % (64 / kRows);
+      if (bi == 0 && tid == 128 && t + 1 < my_tiles) prefetch_tile(t + 1);
+      const int tq = g + t * nqgroups;
+      const int64_t q0 = (int64_t)tq * kTile + half * 64 + bi * kRows;
+      const int64_t off = ((int64_t)tq * nptiles + pt) * (int64_t)(kTile * kTile) +
+                          (int64_t)(half * 64 + bi * kRows) * kTile + lq * 32 + lane;
+      const int live_n = (int)max((int64_t)0, min((int64_t)kRows, (int64_t)n - q0));
+#pragma unroll
+      for (int i = 0; i < kRows; ++i) {
+        const bool live = i < live_n;
+        av[i] = live ? __ldcs(A + off + i * kTile) : __int_as_float(0x7fffffff);
+        yv[i] = live ? __ldcs(Y + off + i * kTile) : 0.f;
+      }
+    };
+    // false when the accumulator wait ran out
+    auto process = [&](int j, const float (&av)[kRows], const float (&yv)[kRows]) -> bool {
+      const int t = j / (64 / kRows), bi = j % (64 / kRows);
       const int b = t & 1;
-      if (tid == 128 && t + 1 < my_tiles) prefetch_tile(t + 1);
-      if (!mbar_wait(barAccFull + b, (uint32_t)((t / 2) & 1))) { *abort_flag = 1; break; }
-      fence_after_sync();
-      const int64_t q0 = (int64_t)(g + t * nqgroups) * kTile + half * 64;
-      // this tile's 64 KB block of each panel: rows q of 128 slots
-      const int64_t tile_base = ((int64_t)(g + t * nqgroups) * nptiles + pt) * (int64_t)(kTile * kTile);
-#pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 32) {
-        const float* ap = A + tile_base + (int64_t)(half * 64 + c0) * kTile + lq * 32 + lane;
-        const float* yp = Y + tile_base + (int64_t)(half * 64 + c0) * kTile + lq * 32 + lane;
-        const int live_n = (int)max((int64_t)0, min((int64_t)32, (int64_t)n - (q0 + c0)));
-        float av[32], yv[32];
+      if (bi == 0) {
+        if (!mbar_wait(barAccFull + b, (uint32_t)((t / 2) & 1))) return false;
+        fence_after_sync();
+      }
+      const int tq = g + t * nqgroups;
+      float* yp = Y + ((int64_t)tq * nptiles + pt) * (int64_t)(kTile * kTile) +
+                  (int64_t)(half * 64 + bi * kRows) * kTile + lq * 32 + lane;
+      float x[kRows];
+      tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * kTile + half * 64 + bi * kRows), x);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const bool live = i < live_n;
-          av[i] = live ? __ldcs(ap + i * kTile) : __int_as_float(0x7fffffff);
-          yv[i] = live ? __ldcs(yp + i * kTile) : 0.f;
-        }
-        float x[32];
-        {
-          float h0[16], h1[16];
-          const uint32_t taddr = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * kTile + half * 64 + c0);
-          tmem_ld16(taddr, h0);
-          tmem_ld16(taddr + 16, h1);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) { x[i] = h0[i]; x[16 + i] = h1[i]; }
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (!isnan(av[i])) {  // observed (and q < n): the update of eq. (4)
-            const float d = av[i] - x[i];
-            const float yn = fmaf(delta, d, yv[i]);
-            acc_d2.add_sq(d);
-            acc_abs.add(fabsf(d));
-            acc_y2.add_sq(yn);
-            bad |= !isfinite(yn);
-            __stcs(const_cast<float*>(yp) + i * kTile, yn);
-          }
+      for (int i = 0; i < kRows; ++i) {
+        if (!isnan(av[i])) {  // observed (and q < n): the update of eq. (4)
+          const float d = av[i] - x[i];
+          const float yn = fmaf(delta, d, yv[i]);
+          acc_d2.add_sq(d);
+          acc_abs.add(fabsf(d));
+          acc_y2.add_sq(yn);
+          bad |= !isfinite(yn);
+          __stcs(yp + i * kTile, yn);
         }
       }
-      fence_before_sync();
-      mbar_arrive(barAccEmpty + b);
+      if (bi == 64 / kRows - 1) {
+        fence_before_sync();
+        mbar_arrive(barAccEmpty + b);
+      }
+      return true;
+    };
+    float a0[kRows], y0[kRows], a1[kRows], y1[kRows];
+    if (nb > 0) load_batch(0, a0, y0);
+    for (int j = 0; j < nb && !*abort_flag; j += 2) {
+      if (j + 1 < nb) load_batch(j + 1, a1, y1);
+      if (!process(j, a0, y0)) { *abort_flag = 1; break; }
+      if (j + 1 < nb) {
+        if (j + 2 < nb) load_batch(j + 2, a0, y0);
+        if (!process(j + 1, a1, y1)) { *abort_flag = 1; break; }
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_NONFINITE);

@@ -49,10 +49,14 @@ svt_status launch_scatter(int64_t count, const int32_t* perm, const T* src, T* d
 // and tails[c] = the row left in the tail slot, or -1.
 template <typename TD>
 void spmm_slots(void* scratch, int64_t nnz, int w, TD** part, int64_t* ldp, int32_t** tails);
-// out[tails[c]] = tail(c) + head(c + 1) + ... for every chunk c with a tail, in chunk order
+// out[tails[c]] = tail(c) + head(c + 1) + ... for every chunk c with a tail: rows spanning
+// more chunks than a segment are summed by segments (each in chunk order, their sums in
+// segment order), which uses the free tail slots of the segments' first chunks.
+// chunk_row (may be null) holds each chunk's first row.
 template <typename TD>
-svt_status spmm_fixup(int64_t nnz, const int32_t* ptr, const TD* part, int64_t ldp,
-                      const int32_t* tails, int w, TD* out, int64_t ldo, cudaStream_t s);
+svt_status spmm_fixup(int64_t nnz, int64_t nrows, const int32_t* ptr, const int32_t* chunk_row,
+                      TD* part, int64_t ldp, const int32_t* tails, int w, TD* out, int64_t ldo,
+                      cudaStream_t s);
 
 // lift_tc.cu ------------------------------------------------------------------
 // C (M x N, binary32, ldc) = A (M x K, binary32, lda) B (K x N, binary64, ldb) on the
@@ -114,16 +118,23 @@ svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work,
 // Per-device set-up of the eigensolver kernels (shared-memory limits); call it before a
 // stream capture that records eig_start_clusters.
 svt_status eig_prepare();
-// After a rejected eig_refine from that start: diagonalise the clusters of pairs that
-// X^T G X still couples, rotate X, refine again with the same acceptance test.
+// After a rejected eig_refine (from any start): diagonalise the clusters of pairs that
+// X^T G X still couples, rotate X, refine again with the same acceptance test.  x_alt
+// tells where the preceding refinement left X (see eig_refine); this one leaves it at
+// eig_x_alt(0, refine_steps).
 svt_status eig_refine_clusters_again(int r, const double* G, int64_t ldg, double* lam, double* Ub,
-                                     int64_t ldu, double* work, int refine_steps, cudaStream_t s,
-                                     int* status, double tol);
+                                     int64_t ldu, double* work, int x_alt, int refine_steps,
+                                     cudaStream_t s, int* status, double tol);
+// Ogita-Aishima steps from the start X in the scratch; the refined X alternates between
+// two scratch buffers step by step: it starts in the second one when start_alt, and ends
+// in the one eig_x_alt(start_alt, refine_steps) names, where a further call can resume.
 svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
                       double* work, int refine_steps, cudaStream_t s, int* check_status = nullptr,
-                      double check_tol = 0.0);
+                      double check_tol = 0.0, int start_alt = 0);
+inline int eig_x_alt(int start_alt, int steps) { return (start_alt ^ steps) & 1; }
 
 // update.cu -------------------------------------------------------------------
+
 size_t reduce_scratch();
 // sum of squares of x[0..count) (binary64 result into *out, device)
 template <typename T>

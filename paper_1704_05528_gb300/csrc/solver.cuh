@@ -156,11 +156,13 @@ inline double gemm_bytes(int64_t M, int p, int q, int sv, bool reads_c) {
 
 constexpr double kExhaustedRel = 1e-7;
 constexpr uint32_t kPowerSeedIter = 0xFFFFFFFFu;
-// Ogita-Aishima steps after the binary32 Jacobi: each squares the eigenvector error
-// (about 1e-7 after Jacobi), so one step reaches binary32-path accuracy and two reach
-// binary64.
+// Ogita-Aishima steps after the binary32 Jacobi: each squares the first-order coupling
+// of a pair.  The Jacobi's rounding is relative to the largest eigenvalue, so the coupling
+// it leaves is about 1e-7 for the large eigenvalues but up to 1e-2 for small ones a short
+// distance apart: one step suffices for binary32 results, three reach binary64 (the
+// acceptance test then adds steps where they are still needed).
 template <typename T>
-constexpr int refine_steps() { return sizeof(T) == 8 ? 2 : 1; }
+constexpr int refine_steps() { return sizeof(T) == 8 ? 3 : 1; }
 // From the near-diagonal start of a recycled basis (couplings below 0.02 of their gaps)
 // the error falls as 1e-4, 1e-8, 1e-16: three steps for binary32 results, four for binary64.
 template <typename T>
@@ -457,6 +459,63 @@ enum class EigFrom {
 };
 
 // svt(B): eigen-decomposition of G = B B^T = (B^T)^T B^T (formed here when gram is set),
+// Reads the acceptance status of the last checked refinement (flags[3]).
+template <typename T>
+svt_status eig_status(Work<T>& W, int* status) {
+  SVT_CUDA(cudaMemcpyAsync(status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, W.s));
+  SVT_CUDA(cudaStreamSynchronize(W.s));
+  return SVT_OK;
+}
+
+// Eigenpairs of G (r x r, in W.G) from the full binary32 Jacobi, refined in binary64 until
+// the acceptance test passes.  The Jacobi's rounding is relative to the largest
+// eigenvalue, so the first-order coupling it leaves between two small eigenvalues a short
+// distance apart can be close to the refinement's limit of 0.1: such pairs need more
+// than the steps that suffice for the large ones, and are given up to four more.  Pairs
+// coupled beyond that limit (eigenvalues that agree to about 4e-7 of the largest) are
+// clusters for the refinement; they are diagonalised in the refined basis by the cluster
+// pass, and refined again.
+template <typename T>
+svt_status eig_from_jacobi(Work<T>& W, int r) {
+  cudaStream_t st = W.s;
+  int* fl3 = reinterpret_cast<int*>(W.flags + 3);
+  {
+    SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
+    SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2), W.flags + 4));
+  }
+  int alt = 0;
+  auto refine = [&](int steps) -> svt_status {
+    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, steps, st, fl3, near_diagonal_tol<T>(), alt));
+    alt = eig_x_alt(alt, steps);
+    return SVT_OK;
+  };
+  int status = 0;
+  SVT_TRY(refine(refine_steps<T>()));
+  SVT_TRY(eig_status(W, &status));
+  for (int round = 0; round < 2 && status != 0; ++round) {
+    prof_count("eig_jacobi_more_steps");
+    SVT_TRY(refine(2));
+    SVT_TRY(eig_status(W, &status));
+  }
+  if (status != 0) {
+    prof_count("eig_jacobi_clusters");
+    {
+      SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
+      SVT_TRY(eig_refine_clusters_again(r, W.G, r, W.lam, W.Ub, r, W.eigw, alt, 2, st, fl3,
+                                        near_diagonal_tol<T>()));
+    }
+    alt = eig_x_alt(0, 2);
+    SVT_TRY(eig_status(W, &status));
+    for (int round = 0; round < 2 && status != 0; ++round) {
+      SVT_TRY(refine(2));
+      SVT_TRY(eig_status(W, &status));
+    }
+    if (status != 0) prof_count("eig_jacobi_unresolved");
+  }
+  return SVT_OK;
+}
+
 // U = Q U_B and sigma on the host.  A purely recycled basis (no new block) leaves G
 // nearly diagonal: the binary64 refinement starts from the identity with the coupled
 // clusters diagonalised, and the result is accepted only if no coupled pair was left;
@@ -497,23 +556,16 @@ svt_status eig_finish(Work<T>& W, T* Q, int r, T* Unew, EigFrom from, bool gram,
     prof_count("eig_start_rejected");
     {
       SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
-      SVT_TRY(eig_refine_clusters_again(r, W.G, r, W.lam, W.Ub, r, W.eigw, 2, st,
-                                        reinterpret_cast<int*>(W.flags + 3),
-                                        near_diagonal_tol<T>()));
+      SVT_TRY(eig_refine_clusters_again(r, W.G, r, W.lam, W.Ub, r, W.eigw,
+                                        eig_x_alt(0, near_diagonal_steps<T>()), 2, st,
+                                        reinterpret_cast<int*>(W.flags + 3), near_diagonal_tol<T>()));
     }
     SVT_CUDA(cudaMemcpyAsync(&status, W.flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     SVT_CUDA(cudaStreamSynchronize(st));
     if (status != 0) prof_count("eig_start_rejected_twice");
     near_diagonal = status == 0;  // else redo from the full Jacobi
   }
-  if (!near_diagonal) {
-    {
-      SVT_PROF("eig_jacobi32", 8.0 * r * r, st);
-      SVT_TRY(eig_start(r, W.G, r, W.eigw, st, reinterpret_cast<int*>(W.flags + 2), W.flags + 4));
-    }
-    SVT_PROF("eig_refine64", 8.0 * 3 * r * r, st);
-    SVT_TRY(eig_refine(r, W.G, r, W.lam, W.Ub, r, W.eigw, refine_steps<T>(), st));
-  }
+  if (!near_diagonal) SVT_TRY(eig_from_jacobi<T>(W, r));
   std::vector<double> lam(r);
   SVT_CUDA(cudaMemcpyAsync(lam.data(), W.lam, r * sizeof(double), cudaMemcpyDeviceToHost, st));
   // U = Q U_B (all r columns are recycled)

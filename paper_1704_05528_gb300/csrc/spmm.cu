@@ -26,6 +26,17 @@ template <> struct VecT<double, 2> { using type = double2; };
 template <typename T> struct VecT<T, 1> { using type = T; };
 
 template <typename T, int VEC>
+__device__ __forceinline__ void store_vec(T* p, const T (&v)[VEC]) {
+  if constexpr (VEC == 1) {
+    p[0] = v[0];
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <typename T, int VEC>
 __device__ __forceinline__ void load_vec(const T* p, T (&v)[VEC]) {
   if constexpr (VEC == 1) {
     v[0] = p[0];
@@ -141,15 +152,86 @@ k_spmm_chunked(int64_t nrows, int64_t nnz, int64_t C, const int32_t* __restrict_
   if (lane == 0) tail_row[chunk] = my_tail;
 }
 
-// out[r] = tail(c) + head(c+1) + ... + head(c_last) for the row r left in chunk c's tail;
-// one warp per chunk, lanes over vectors of VEC columns (partial rows are 16-byte aligned
-// with a padded leading dimension).  A row can span hundreds of chunks: eight independent
-// loads are issued per step and added in chunk order (the same order as one at a time).
+// out[r] = tail(c) + head(c+1) + ... + head(c_last) for the row r left in chunk c's tail,
+// in two passes so that no warp walks a long row alone: a row spanning more than kFixSeg
+// chunks (a popular column spans hundreds) is cut into segments of kFixSeg chunks, each
+// summed in chunk order by the warp of its first chunk, whose own tail slot is free (the
+// chunk lies inside that row), and the second pass adds tail(c) and the segment sums in
+// segment order.  Rows spanning at most kFixSeg chunks are summed in chunk order by the
+// first pass.  One warp per chunk, lanes over vectors of VEC columns (partial rows are
+// 16-byte aligned with a padded leading dimension); eight independent loads per step.
+constexpr int kFixSeg = 16;
+
+template <typename TD, int VEC>
+__device__ __forceinline__ void add_heads(const TD* __restrict__ part, int64_t ldp, int c,
+                                          int64_t k0, int64_t k1, TD (&s)[VEC]) {
+  int64_t k = k0;
+  for (; k + 8 <= k1 + 1; k += 8) {
+    TD v[8][VEC];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) load_vec<TD, VEC>(part + (2 * (k + j)) * ldp + c, v[j]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int b = 0; b < VEC; ++b) s[b] += v[j][b];
+  }
+  for (; k <= k1; ++k) {
+    TD v[VEC];
+    load_vec<TD, VEC>(part + (2 * k) * ldp + c, v);
+#pragma unroll
+    for (int b = 0; b < VEC; ++b) s[b] += v[b];
+  }
+}
+
 template <typename TD>
 __global__ void __launch_bounds__(256)
-k_spmm_fixup(int64_t nchunks, int64_t C, const int32_t* __restrict__ ptr,
-             const TD* __restrict__ part, int64_t ldp, const int32_t* __restrict__ tail_row, int w,
-             TD* __restrict__ out, int64_t ldo) {
+k_spmm_fixup(int64_t nchunks, int64_t C, int64_t nrows, const int32_t* __restrict__ ptr,
+             const int32_t* __restrict__ chunk_row, TD* __restrict__ part, int64_t ldp,
+             const int32_t* __restrict__ tail_row, int w, TD* __restrict__ out, int64_t ldo) {
+  constexpr int VEC = sizeof(TD) == 4 ? 4 : 2;
+  const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (chunk >= nchunks) return;
+  const int nvec = (w + VEC - 1) / VEC;
+  const int32_t r = tail_row[chunk];
+  if (r >= 0) {  // a row starts here and continues: sum it now if it is short
+    const int64_t c_last = ((int64_t)ptr[r + 1] - 1) / C;
+    if (c_last - chunk > kFixSeg) return;  // long: second pass
+    for (int cv = lane; cv < nvec; cv += 32) {
+      const int c = cv * VEC;
+      TD s[VEC];
+      load_vec<TD, VEC>(part + (2 * chunk + 1) * ldp + c, s);
+      add_heads<TD, VEC>(part, ldp, c, chunk + 1, c_last, s);
+#pragma unroll
+      for (int b = 0; b < VEC; ++b)
+        if (c + b < w) out[(int64_t)r * ldo + c + b] = s[b];
+    }
+    return;
+  }
+  // the first chunk of a segment of a long row that started before this chunk?
+  const int64_t beg = chunk * C;
+  const int64_t hr = chunk_row ? chunk_row[chunk] : chunk_first_row(ptr, nrows, beg);
+  if (hr >= nrows || (int64_t)ptr[hr] >= beg) return;
+  const int64_t c0 = (int64_t)ptr[hr] / C;
+  const int64_t c_last = ((int64_t)ptr[hr + 1] - 1) / C;
+  if (c_last - c0 <= kFixSeg || (chunk - (c0 + 1)) % kFixSeg != 0 || chunk >= c_last) return;
+  const int64_t k1 = chunk + kFixSeg - 1 < c_last ? chunk + kFixSeg - 1 : c_last;
+  for (int cv = lane; cv < nvec; cv += 32) {
+    const int c = cv * VEC;
+    TD s[VEC];
+#pragma unroll
+    for (int b = 0; b < VEC; ++b) s[b] = TD(0);
+    add_heads<TD, VEC>(part, ldp, c, chunk, k1, s);
+    store_vec<TD, VEC>(part + (2 * chunk + 1) * ldp + c, s);  // this chunk's free tail slot
+  }
+}
+
+// Second pass: out[r] = tail(c) + the segment sums in order, for the long rows.
+template <typename TD>
+__global__ void __launch_bounds__(256)
+k_spmm_fixup_long(int64_t nchunks, int64_t C, const int32_t* __restrict__ ptr,
+                  const TD* __restrict__ part, int64_t ldp, const int32_t* __restrict__ tail_row,
+                  int w, TD* __restrict__ out, int64_t ldo) {
   constexpr int VEC = sizeof(TD) == 4 ? 4 : 2;
   const int64_t chunk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -157,24 +239,26 @@ k_spmm_fixup(int64_t nchunks, int64_t C, const int32_t* __restrict__ ptr,
   const int32_t r = tail_row[chunk];
   if (r < 0) return;
   const int64_t c_last = ((int64_t)ptr[r + 1] - 1) / C;
+  if (c_last - chunk <= kFixSeg) return;
   const int nvec = (w + VEC - 1) / VEC;
   for (int cv = lane; cv < nvec; cv += 32) {
     const int c = cv * VEC;
     TD s[VEC];
     load_vec<TD, VEC>(part + (2 * chunk + 1) * ldp + c, s);
-    int64_t k = chunk + 1;
-    for (; k + 8 <= c_last + 1; k += 8) {
+    int64_t ks = chunk + 1;
+    for (; ks + 8 * kFixSeg <= c_last; ks += 8 * kFixSeg) {  // eight segments in flight
       TD v[8][VEC];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) load_vec<TD, VEC>(part + (2 * (k + j)) * ldp + c, v[j]);
+      for (int j = 0; j < 8; ++j) load_vec<TD, VEC>(part + (2 * (ks + j * kFixSeg) + 1) * ldp + c, v[j]);
 #pragma unroll
       for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int b = 0; b < VEC; ++b) s[b] += v[j][b];
     }
-    for (; k <= c_last; ++k) {
+    for (; ks <= c_last; ks += kFixSeg) {
       TD v[VEC];
-      load_vec<TD, VEC>(part + (2 * k) * ldp + c, v);
+      // a segment starting at the row's last chunk is that chunk's head alone
+      load_vec<TD, VEC>(part + (ks < c_last ? 2 * ks + 1 : 2 * ks) * ldp + c, v);
 #pragma unroll
       for (int b = 0; b < VEC; ++b) s[b] += v[b];
     }
@@ -232,7 +316,9 @@ svt_status run_chunked(int64_t nrows, int64_t nnz, const int32_t* ptr, const int
                                                               out, ldo, part, ldp, tails, nchunks,
                                                               chunk_row);
   SVT_LAUNCH_CHECK();
-  k_spmm_fixup<TD><<<blocks, 256, 0, s>>>(nchunks, C, ptr, part, ldp, tails, w, out, ldo);
+  k_spmm_fixup<TD><<<blocks, 256, 0, s>>>(nchunks, C, nrows, ptr, chunk_row, part, ldp, tails, w, out, ldo);
+  SVT_LAUNCH_CHECK();
+  k_spmm_fixup_long<TD><<<blocks, 256, 0, s>>>(nchunks, C, ptr, part, ldp, tails, w, out, ldo);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -339,13 +425,16 @@ void spmm_slots(void* scratch, int64_t nnz, int w, TD** part, int64_t* ldp, int3
 }
 
 template <typename TD>
-svt_status spmm_fixup(int64_t nnz, const int32_t* ptr, const TD* part, int64_t ldp,
-                      const int32_t* tails, int w, TD* out, int64_t ldo, cudaStream_t s) {
+svt_status spmm_fixup(int64_t nnz, int64_t nrows, const int32_t* ptr, const int32_t* chunk_row,
+                      TD* part, int64_t ldp, const int32_t* tails, int w, TD* out, int64_t ldo,
+                      cudaStream_t s) {
   if (nnz <= 0 || w <= 0) return SVT_OK;
   const int64_t C = chunk_size(nnz);
   const int64_t nchunks = ceil_div(nnz, C);
-  k_spmm_fixup<TD><<<(int)ceil_div(nchunks, 8), 256, 0, s>>>(nchunks, C, ptr, part, ldp, tails, w,
-                                                              out, ldo);
+  const int blocks = (int)ceil_div(nchunks, 8);
+  k_spmm_fixup<TD><<<blocks, 256, 0, s>>>(nchunks, C, nrows, ptr, chunk_row, part, ldp, tails, w, out, ldo);
+  SVT_LAUNCH_CHECK();
+  k_spmm_fixup_long<TD><<<blocks, 256, 0, s>>>(nchunks, C, ptr, part, ldp, tails, w, out, ldo);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -367,9 +456,9 @@ template svt_status launch_scatter<float>(int64_t, const int32_t*, const float*,
                                           cudaStream_t);
 template void spmm_slots<double>(void*, int64_t, int, double**, int64_t*, int32_t**);
 template void spmm_slots<float>(void*, int64_t, int, float**, int64_t*, int32_t**);
-template svt_status spmm_fixup<double>(int64_t, const int32_t*, const double*, int64_t,
-                                       const int32_t*, int, double*, int64_t, cudaStream_t);
-template svt_status spmm_fixup<float>(int64_t, const int32_t*, const float*, int64_t,
-                                      const int32_t*, int, float*, int64_t, cudaStream_t);
+template svt_status spmm_fixup<double>(int64_t, int64_t, const int32_t*, const int32_t*, double*,
+                                       int64_t, const int32_t*, int, double*, int64_t, cudaStream_t);
+template svt_status spmm_fixup<float>(int64_t, int64_t, const int32_t*, const int32_t*, float*,
+                                      int64_t, const int32_t*, int, float*, int64_t, cudaStream_t);
 
 }  // namespace svt

@@ -18,9 +18,8 @@
 //  - the first call on a device looks up the array's device address there
 //    (cudaGetSymbolAddress, with that device current) and caches it for the process; a
 //    cudaDeviceReset would leave that cached address stale, so resetting a device while
-//    this library is in use is not supported;
-//  - like svt_spmm, the call waits for its stream before returning, so it cannot be
-//    recorded into a stream capture.
+//    this library is in use is not supported; that first call belongs before any stream
+//    capture.
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -498,7 +498,7 @@ svt_status run_recycle(const svt_pattern* p, const T* U, int64_t ldu, int r, con
       (int32_t)p->n, (int32_t)z, (int32_t)C, (int32_t)nchunks, p->col_ptr, p->row_idx, p->chunk_row_csc, U, ldu, r, W, ldw, k, a, y,
       (T)delta, bt, ldb, slots, ldp, tails, part, flags);
   SVT_LAUNCH_CHECK();
-  return spmm_fixup<T>(z, p->col_ptr, slots, ldp, tails, r, bt, ldb, s);
+  return spmm_fixup<T>(z, p->n, p->col_ptr, p->chunk_row_csc, slots, ldp, tails, r, bt, ldb, s);
 }
 
 // Up to four vectors of U's row per lane, two entries in flight per group, as few lanes

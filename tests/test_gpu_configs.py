@@ -127,37 +127,24 @@ def test_config_lowrank500_full_length(env, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_config_image512(env, prec):
-    """512 x 512 power-law image shape, 50% observed, step 1.9, ranks growing towards the
-    512 cap (so the grid Jacobi runs).  On this workload R4SVD's rank-revealing
-    approximation of D_tau amplifies rounding: the binary64 GPU path and the binary64
-    oracle agree to 1e-12 through iteration 35, after which their difference grows by
-    about 5% per iteration (to 1e-2 after 500 iterations).  Trajectory parity is therefore
-    checked over the first 30 iterations, at the usual bars.  Over the whole 500-iteration
-    solve, the binary64 path's mean residual over the last 100 iterations must stay within
-    a factor of two of the oracle's; the mixed-precision path, whose binary32 rounding is
-    amplified the same way from the first iterations on, must keep converging (its final
-    residual below a tenth of its residual at iteration 50).  Both levels are printed."""
+def test_config_image512_full_length(env, prec):
+    """512 x 512 power-law image shape, 50% observed, step 1.9: the whole 500-iteration
+    solve, with revealed ranks growing to the 512 cap (so the grid Jacobi and the cluster
+    passes of the eigensolver run).  Both precisions follow the oracle's trajectory
+    (revealed ranks, block counts, cooling decisions; kept counts up to rounding ties),
+    and every iteration's relative residual agrees with the oracle's to 1e-8 (binary64)
+    or 1e-3 (mixed), on top of the completion bars."""
     svt, torch = env
     w = _workload("image512")
-    ref = _oracle("image512", w, 30)
-    got = _gpu(svt, torch, w, 30, prec)
-    if prec == "fp64":
-        _same_trajectory(ref, got, w.tau)
-    _compare("image512 (30 iterations)", w, ref, got, prec)
-    ref_full = _oracle("image512", w, w.maxit)
-    got_full = _gpu(svt, torch, w, w.maxit, prec)
-    tail = lambda r: float(np.mean([e["rel_residual"] for e in r.log[-100:]]))
-    t_ref, t_got = tail(ref_full), tail(got_full)
-    e_obs = _rel(_completed(got_full, ref_full.pattern.csr_rows(), ref_full.pattern.col_idx),
-                 _completed(ref_full, ref_full.pattern.csr_rows(), ref_full.pattern.col_idx))
-    print(f"\nimage512 {prec}, 500 iterations: mean residual of the last 100 {t_got:.4e} (oracle "
-          f"{t_ref:.4e}), final {got_full.rel_residual:.4e} ({ref_full.rel_residual:.4e}); relative "
-          f"difference of the completions {e_obs:.3e}")
-    if prec == "fp64":
-        assert 0.5 < t_got / t_ref < 2.0
-    else:
-        assert got_full.rel_residual < 0.1 * got_full.log[49]["rel_residual"]
+    ref = _oracle("image512", w, w.maxit)
+    got = _gpu(svt, torch, w, w.maxit, prec)
+    _same_trajectory(ref, got, w.tau, tie=1e-9 if prec == "fp64" else 1e-5)
+    res_g = np.array([e["rel_residual"] for e in got.log])
+    res_o = np.array([e["rel_residual"] for e in ref.log])
+    worst = float(np.max(np.abs(res_g - res_o) / res_o))
+    print(f"\nimage512 {prec}: largest relative difference of a per-iteration residual {worst:.2e}")
+    assert worst < (1e-8 if prec == "fp64" else 1e-3)
+    _compare("image512", w, ref, got, prec)
 
 
 def test_config_ratings6040_full_size_mixed(env):
