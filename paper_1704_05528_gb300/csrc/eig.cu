@@ -379,7 +379,7 @@ size_t cluster_smem_bytes() {
 
 __global__ void __launch_bounds__(1024)
 k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __restrict__ X,
-                int64_t ldx, int* __restrict__ status, int identity_on_fail) {
+                int64_t ldx, int* __restrict__ status, int identity_on_fail, int shift) {
   extern __shared__ int csm[];
   int* label = csm;                    // 1024
   int* cnt = label + 1024;             // 1024
@@ -462,10 +462,12 @@ k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __rest
         sz += __popc(m);
       }
       __syncwarp();
-      // The block is shifted by the mean of its diagonal (in binary64) before it is
-      // rounded to binary32: a cluster's eigenvalues agree in their leading digits, and
-      // the shift keeps the digits that tell them apart.  Rotations do not depend on it.
-      double mu = lane < sz ? G[(int64_t)mb[lane] * ldg + mb[lane]] : 0.0;
+      // With `shift` (the cluster pass after a refinement, whose clusters are pairs that
+      // agree to binary32 rounding) the block is shifted by the mean of its diagonal (in
+      // binary64) before it is rounded to binary32: a cluster's eigenvalues agree in their
+      // leading digits, and the shift keeps the digits that tell them apart.  Rotations do
+      // not depend on it.
+      double mu = lane < sz && shift ? G[(int64_t)mb[lane] * ldg + mb[lane]] : 0.0;
       for (int o = 16; o > 0; o >>= 1) mu += __shfl_xor_sync(0xffffffffu, mu, o);
       mu /= (double)sz;
       for (int a = 0; a < sz; ++a)
@@ -531,7 +533,7 @@ k_cluster_start(int r, const double* __restrict__ G, int64_t ldg, double* __rest
     // the shift of the warp clusters above: every warp forms the same sum (lanes over
     // members, a fixed shuffle tree, then the lanes' partial sums in order)
     double mu = 0.0;
-    for (int a0 = 0; a0 < sz; a0 += 32) {
+    for (int a0 = 0; a0 < sz && shift; a0 += 32) {
       double v = a0 + lane < sz ? G[(int64_t)bigm[a0 + lane] * ldg + bigm[a0 + lane]] : 0.0;
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       mu += v;
@@ -805,7 +807,7 @@ svt_status eig_start_clusters(int r, const double* G, int64_t ldg, double* work,
   const size_t smem = cluster_smem_bytes();
   SVT_TRY(eig_prepare());
   k_cluster_start<<<1, 1024, smem, s>>>(r, G, ldg, w.XP, 2 * (int64_t)r, status,
-                                        identity_on_fail ? 1 : 0);
+                                        identity_on_fail ? 1 : 0, 0);
   SVT_LAUNCH_CHECK();
   return SVT_OK;
 }
@@ -821,7 +823,7 @@ svt_status eig_refine_clusters_again(int r, const double* G, int64_t ldg, double
   // if a cluster is too large: the check below then fails again)
   const size_t smem = cluster_smem_bytes();
   SVT_TRY(eig_prepare());
-  k_cluster_start<<<1, 1024, smem, s>>>(r, w.CS + r, l2, w.E, r, status, 1);
+  k_cluster_start<<<1, 1024, smem, s>>>(r, w.CS + r, l2, w.E, r, status, 1, 1);
   SVT_LAUNCH_CHECK();
   // X <- X X1, into XP (where the refinement starts)
   const dim3 grid((unsigned)ceil_div(r, kSgTile), (unsigned)ceil_div(r, kSgTile));
