@@ -161,17 +161,15 @@ __global__ void k_assemble(int64_t z, const int32_t* __restrict__ full_src, cons
   }
 }
 
-// TF32 high and low parts of W (n x k, ldw), written n x 128 (K-major, zero beyond k).
-__global__ void k_split_w(int64_t n, int k, const float* __restrict__ W, int64_t ldw,
-                          float* __restrict__ hi, float* __restrict__ lo) {
+// W (n x k, ldw) copied to n x 128 (K-major, zero beyond k), for a W whose rows a tensor
+// map cannot address directly (leading dimension not a multiple of four values).
+__global__ void k_pad_w(int64_t n, int k, const float* __restrict__ W, int64_t ldw,
+                        float* __restrict__ out) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * kKMax;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = t >> 7;
     const int j = (int)(t & (kKMax - 1));
-    const float w = j < k ? W[q * ldw + j] : 0.f;
-    const float h = tf32_round(w);
-    hi[t] = h;
-    lo[t] = w - h;
+    out[t] = j < k ? W[q * ldw + j] : 0.f;
   }
 }
 
@@ -223,13 +221,15 @@ constexpr uint32_t kUpdTmemCols = 256;                  // two 128-column accumu
 // memory, and the q tiles g, g + G, ... of W streamed by TMA.  The MMA computes X[slot, q]
 // (M = 128 slots, N = 128 q, K = k), so a tensor-memory lane is a slot and the 32 lanes of
 // a warp read and write 32 consecutive slots of one panel row q: 128 contiguous bytes.
-// Warp 0 loads, warp 1 issues the MMAs into one of two accumulators, warps 4-11 apply the
-// update from the other (warp 4 + 4h + i: lanes 32i .. 32i + 31, q columns 64h .. 64h + 63).
+// Warp 0 loads (chunks of W as they are, zero beyond k), warps 2-3 split each chunk in
+// place into its TF32 high part and a low-part copy, warp 1 issues the MMAs into one of two
+// accumulators, warps 4-11 apply the update from the other (warp 4 + 4h + i: lanes
+// 32i .. 32i + 31, q columns 64h .. 64h + 63).
 constexpr int kUpdThreads = 384;
 template <int NK>
 __global__ void __launch_bounds__(kUpdThreads, 1)
-k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensorMap mWhi,
-              const __grid_constant__ CUtensorMap mWlo, const __grid_constant__ CUtensorMap mUhi,
+k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensorMap mW,
+              const __grid_constant__ CUtensorMap mUhi,
               const __grid_constant__ CUtensorMap mUlo, const float* __restrict__ A,
               float* __restrict__ Y, int64_t ldd, float delta, double* __restrict__ part,
               unsigned* __restrict__ flags, unsigned* __restrict__ status) {
@@ -245,7 +245,8 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
   uint64_t* barAccFull = barEmpty + kUpdStages;      // [2]
   uint64_t* barAccEmpty = barAccFull + 2;            // [2]
   uint64_t* barDrain = barAccEmpty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barDrain + 1);
+  uint64_t* barSplit = barDrain + 1;                 // [S] (64 arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barSplit + kUpdStages);
   __shared__ int s_abort;
   __shared__ double s_sum[8][3];
   volatile int* abort_flag = &s_abort;
@@ -257,7 +258,11 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
   if (tid == 0) {
     s_abort = 0;
     mbar_init(barB, 1);
-    for (int s = 0; s < kUpdStages; ++s) { mbar_init(barFull + s, 1); mbar_init(barEmpty + s, 1); }
+    for (int s = 0; s < kUpdStages; ++s) {
+      mbar_init(barFull + s, 1);
+      mbar_init(barEmpty + s, 1);
+      mbar_init(barSplit + s, 64);
+    }
     for (int b = 0; b < 2; ++b) { mbar_init(barAccFull + b, 1); mbar_init(barAccEmpty + b, 256); }
     mbar_init(barDrain, 1);
     mbar_init_fence();
@@ -285,9 +290,8 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
           break;
         }
         const int tile = g + (j / NK) * nqgroups, c = j % NK;
-        mbar_expect_tx(barFull + s, (uint32_t)(2 * kChunkBytes));
-        tma_load_2d(sA + s * 2 * kChunkBytes, &mWhi, c * kKC, tile * kTile, barFull + s);
-        tma_load_2d(sA + s * 2 * kChunkBytes + kChunkBytes, &mWlo, c * kKC, tile * kTile, barFull + s);
+        mbar_expect_tx(barFull + s, (uint32_t)kChunkBytes);
+        tma_load_2d(sA + s * 2 * kChunkBytes, &mW, c * kKC, tile * kTile, barFull + s);
         issued = j + 1;
       }
       // nothing may still land in shared memory when the CTA leaves
@@ -308,7 +312,7 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
         fence_after_sync();
         for (int c = 0; c < NK; ++c, ++j) {
           const int s = j % kUpdStages;
-          if (!mbar_wait(barFull + s, (uint32_t)((j / kUpdStages) & 1))) { *abort_flag = 1; break; }
+          if (!mbar_wait(barSplit + s, (uint32_t)((j / kUpdStages) & 1))) { *abort_flag = 1; break; }
           fence_after_sync();
           const unsigned char* w_hi = sA + s * 2 * kChunkBytes;
           const unsigned char* w_lo = w_hi + kChunkBytes;
@@ -326,6 +330,24 @@ k_core_update(int n, int nptiles, int nqgroups, const __grid_constant__ CUtensor
           if (c == NK - 1) mma_commit(barAccFull + b);
         }
       }
+    }
+  } else if (warp == 2 || warp == 3) {  // split each landed chunk of W into TF32 parts
+    const int t64 = tid - 64;
+    for (int j = 0; j < total && !*abort_flag; ++j) {
+      const int s = j % kUpdStages;
+      if (!mbar_wait(barFull + s, (uint32_t)((j / kUpdStages) & 1))) { *abort_flag = 1; break; }
+      float4* hi4 = reinterpret_cast<float4*>(sA + s * 2 * kChunkBytes);
+      float4* lo4 = reinterpret_cast<float4*>(sA + s * 2 * kChunkBytes + kChunkBytes);
+#pragma unroll 4
+      for (int i = t64; i < kChunkBytes / 16; i += 64) {  // elementwise: the swizzle is the same
+        const float4 x = hi4[i];
+        float4 h;
+        h.x = tf32_round(x.x); h.y = tf32_round(x.y); h.z = tf32_round(x.z); h.w = tf32_round(x.w);
+        hi4[i] = h;
+        lo4[i] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      fence_proxy_async();
+      mbar_arrive(barSplit + s);
     }
   } else if (warp >= 4) {  // epilogue: thread = one slot, 64 q columns per warp
     const int lq = warp & 3, half = (warp - 4) >> 2;
@@ -745,8 +767,7 @@ void core_layout(Arena& a, const CorePlan& plan, int64_t m, int64_t n, int r_cap
   C->y_rest = a.take<float>(zr);
   C->A = a.take<float>(round_up(n, kTile) * ldd);
   C->Y = a.take<float>(round_up(n, kTile) * ldd);
-  C->w_hi = a.take<float>(n * kKMax);
-  C->w_lo = a.take<float>(n * kKMax);
+  C->w_pad = a.take<float>(n * kKMax);
   C->ud_hi = a.take<float>(ldd * kKMax);
   C->ud_lo = a.take<float>(ldd * kKMax);
   C->udt_hi = a.take<float>(kKMax * ldd);
@@ -820,20 +841,29 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
   const int nk = (int)ceil_div(k, kKC);
   const int nptiles = (int)(ldd / kTile);
   const int nq = (int)ceil_div(n, kTile);
+  // W is read by the update kernel through a tensor map (columns beyond k read as zero) and
+  // split into its TF32 parts in shared memory; a W that a map cannot address is copied
+  // into a padded buffer first, and k = 0 maps a zeroed one (X = 0 on the core)
+  const bool w_direct = nk > 0 && ldw % 4 == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
   {
-    SVT_PROF("core_split", 4.0 * (double)(n * k + 2 * n * kKMax + ldd * r + 4 * ldd * kKMax), s);
-    if (nk > 0) {
-      k_split_w<<<egrid(n * kKMax), 256, 0, s>>>(n, k, W, ldw, C.w_hi, C.w_lo);
-      SVT_LAUNCH_CHECK();
+    SVT_PROF("core_split", 4.0 * (double)(ldd * r + 4 * ldd * kKMax) + (w_direct ? 0.0 : 4.0 * (double)(n * k + n * kKMax)), s);
+    if (!w_direct) {
+      if (nk > 0) {
+        k_pad_w<<<egrid(n * kKMax), 256, 0, s>>>(n, k, W, ldw, C.w_pad);
+        SVT_LAUNCH_CHECK();
+      } else {
+        SVT_CUDA(cudaMemsetAsync(C.w_pad, 0, n * kKMax * sizeof(float), s));
+      }
     }
     k_gather_ud<<<dim3((unsigned)ceil_div(ldd, 32), kKMax / 32), 256, 0, s>>>(ldd, k, r, npad, C.slot_row, U, ldu,
                                                                            C.ud_hi, C.ud_lo, C.udt_hi, C.udt_lo);
     SVT_LAUNCH_CHECK();
   }
-  CUtensorMap mWh, mWl, mUh, mUl, mY, mTh, mTl;
+  CUtensorMap mW, mUh, mUl, mY, mTh, mTl;
   const uint64_t rowb = (uint64_t)kKMax * 4;
-  if (!encode_2d(&mWh, C.w_hi, kKMax, (uint64_t)n, rowb, kKC, kTile) ||
-      !encode_2d(&mWl, C.w_lo, kKMax, (uint64_t)n, rowb, kKC, kTile) ||
+  const bool w_ok = w_direct ? encode_2d(&mW, W, (uint64_t)k, (uint64_t)n, (uint64_t)ldw * 4, kKC, kTile)
+                             : encode_2d(&mW, C.w_pad, kKMax, (uint64_t)n, rowb, kKC, kTile);
+  if (!w_ok ||
       !encode_2d(&mUh, C.ud_hi, kKMax, (uint64_t)ldd, rowb, kKC, kTile) ||
       !encode_2d(&mUl, C.ud_lo, kKMax, (uint64_t)ldd, rowb, kKC, kTile) ||
       !encode_panel_4d(&mY, C.Y, ldd / kTile, ceil_div(n, kTile)) ||
@@ -843,14 +873,9 @@ svt_status core_update(const DenseCore& C, const float* U, int64_t ldu, int r, c
   // X on the core and the update (k = 0: X = 0, the update still applies)
   const int nqg = std::max(1, std::min(nq, num_sms() / std::max(nptiles, 1)));
   const int grid1 = nptiles * nqg;
-  if (nk == 0) {
-    // no kept singular value: X = 0 on the core; a zero W keeps one MMA chunk meaningful
-    SVT_CUDA(cudaMemsetAsync(C.w_hi, 0, n * kKMax * sizeof(float), s));
-    SVT_CUDA(cudaMemsetAsync(C.w_lo, 0, n * kKMax * sizeof(float), s));
-  }
 #define SVT_UPD(NK)                                                                                  \
   case NK:                                                                                           \
-    k_core_update<NK><<<grid1, kUpdThreads, kUpdBytes, s>>>((int)n, nptiles, nqg, mWh, mWl, mUh, mUl,  \
+    k_core_update<NK><<<grid1, kUpdThreads, kUpdBytes, s>>>((int)n, nptiles, nqg, mW, mUh, mUl,  \
                                                          C.A, C.Y, ldd, (float)delta, C.part, flags, \
                                                          tc_status);                                 \
     break

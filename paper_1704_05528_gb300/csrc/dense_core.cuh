@@ -32,7 +32,7 @@ struct DenseCore {
   svt_pattern rest;               // views of the arrays above (not owned)
   float *a_rest = nullptr, *y_rest = nullptr;  // observed values and Y of the rest (its CSC order)
   float *A = nullptr, *Y = nullptr;            // n x ldd core panels: A (NaN = unobserved), Y
-  float *w_hi = nullptr, *w_lo = nullptr;      // n x 128: TF32 parts of W
+  float* w_pad = nullptr;                      // n x 128: W zero-padded, where W itself cannot be mapped
   float *ud_hi = nullptr, *ud_lo = nullptr;    // ldd x 128: TF32 parts of the core rows of U
   float *udt_hi = nullptr, *udt_lo = nullptr;  // 128 x ldd: the same, transposed
   double* part = nullptr;                      // per-CTA sums of the core update

@@ -299,8 +299,8 @@ k_oa_update(int r, const double* __restrict__ XP, int64_t l2, const double* __re
 // lam_i = S_ii / C_ii; when `status` is given, the convergence test (*status = 1 when an
 // off-diagonal entry of S = X^T G X exceeds tol times its largest diagonal entry, i.e. a
 // coupled pair was left unresolved, else 0); then the eigenpairs sorted by descending
-// eigenvalue (bitonic network over the next power of two >= r, ties by index) into
-// lam_out and the columns of Ub.
+// eigenvalue (each thread counts the eigenvalues ranked before its own; ties by index)
+// into lam_out and the columns of Ub.
 __global__ void __launch_bounds__(1024)
 k_oa_finish(int r, const double* __restrict__ CS, double tol, int* __restrict__ status,
             const double* __restrict__ X, int64_t ldx, double* __restrict__ lam_out,
@@ -323,31 +323,29 @@ k_oa_finish(int r, const double* __restrict__ CS, double tol, int* __restrict__ 
     }
     if ((t & 31) == 0) { red_off[t >> 5] = off; red_diag[t >> 5] = dg; }
   }
-  int P = 2;
-  while (P < r) P <<= 1;
-  key[t] = t < r ? CS[t * ld + r + t] / CS[t * ld + t] : -INFINITY;
-  idx[t] = t;
+  if (t < r) key[t] = CS[t * ld + r + t] / CS[t * ld + t];
+  idx[t] = t < r ? t : 0;
   __syncthreads();
   if (status && t == 0) {
     double off = red_off[0], dg = red_diag[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { off = fmax(off, red_off[w]); dg = fmax(dg, red_diag[w]); }
     *status = (off <= tol * dg) ? 0 : 1;  // NaN counts as not converged
   }
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const int ixj = t ^ j;
-      if (ixj > t && ixj < P) {
-        const bool desc = (t & k) == 0;
-        const double a = key[t], b = key[ixj];
-        const int ia = idx[t], ib = idx[ixj];
-        const bool a_first = (a > b) || (a == b && ia < ib);
-        if (desc != a_first) {
-          key[t] = b; key[ixj] = a; idx[t] = ib; idx[ixj] = ia;
-        }
-      }
-      __syncthreads();
+  // rank of each eigenvalue: the number of eigenvalues placed before it (larger, or equal
+  // with a smaller index); a NaN ranks first and may share its slot, which the caller
+  // rejects as a non-finite eigenvalue
+  double kt = 0.0;
+  int rank = 0;
+  if (t < r) {
+    kt = key[t];
+    for (int j = 0; j < r; ++j) {
+      const double kj = key[j];
+      rank += (kj > kt) || (kj == kt && j < t);
     }
   }
+  __syncthreads();
+  if (t < r) { idx[rank] = t; key[rank] = kt; }
+  __syncthreads();
   if (t < r) lam_out[t] = key[t];
   // row a of Ub, column j: warp w takes rows w, w + 32, ...; lanes take columns
   for (int a = t >> 5; a < r; a += blockDim.x >> 5)
@@ -367,7 +365,7 @@ k_oa_finish(int r, const double* __restrict__ CS, double tol, int* __restrict__ 
 constexpr double kClusterTol = 0.02;
 constexpr int kClusterMax = 32;
 constexpr int kBigClusterMax = 96;
-constexpr int kClusterWarps = 4;
+constexpr int kClusterWarps = 8;  // warps solving small clusters at once
 constexpr int kMaxEdges = 4096;
 
 size_t cluster_smem_bytes() {
