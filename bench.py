@@ -195,12 +195,15 @@ def load_traffic(kernel):
     e = d.get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_1704_05528_gb300", "csrc", e["source"])
+    sources = e.get("sources") or [e["source"]]
+    digest = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for name in sources:  # in the listed order
+            with open(os.path.join(ROOT, "paper_1704_05528_gb300", "csrc", name), "rb") as f:
+                digest.update(f.read())
     except OSError:
         return None
-    return e["bytes_per_launch"] if h == e.get("source_sha256_16") else None
+    return e["bytes_per_launch"] if digest.hexdigest()[:16] == e.get("source_sha256_16") else None
 
 
 def flush_l2(buf):
