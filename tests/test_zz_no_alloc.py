@@ -152,3 +152,36 @@ def test_noalloc_rejects_short_operands_on_the_host(env):
         svt.spmm_noalloc(P, y[:-1], torch.zeros((P.n, 4), device="cuda", dtype=torch.float64), out)
     with pytest.raises(ValueError):
         svt.spmm(P, y, torch.zeros((P.n, 4), device="cuda", dtype=torch.float64), transpose=True)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed", 2e-6)])
+def test_noalloc_matches_the_oracle_product(env, prec, tol):
+    """The product of Algorithms 2-3 (X = Y Omega, and Y^T Q in the other order) against
+    the binary64 oracle's sparse product on the same pattern and values, with a column
+    spanning many work chunks (a popular column) so that the fix-up's segments run."""
+    import oracle
+    from oracle import fastsvt as OF
+    svt, torch = env
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rng = np.random.default_rng(23)
+    m, n, z = 3000, 700, 60000
+    flat = rng.choice(m * n, size=z, replace=False)
+    rows, cols = (flat // n).astype(np.int32), (flat % n).astype(np.int32)
+    extra = np.setdiff1d(np.arange(m, dtype=np.int64) * n + 5, flat)  # column 5 fully observed
+    rows = np.concatenate([rows, (extra // n).astype(np.int32)])
+    cols = np.concatenate([cols, (extra % n).astype(np.int32)])
+    P = svt.Pattern(m, n, rows, cols)
+    ref_p = oracle.build_pattern(m, n, rows, cols)
+    y = rng.standard_normal(P.nnz)
+    Ys = OF._sparse(ref_p, y)
+    y_dev = torch.from_numpy(y).to(device="cuda", dtype=dt)
+    for transpose, width in ((False, 10), (True, 100)):
+        rows_in, rows_out = (m, n) if transpose else (n, m)
+        W = rng.standard_normal((rows_in, width))
+        W_dev = torch.from_numpy(W).to(device="cuda", dtype=dt)
+        exact = np.asarray((Ys.T @ W) if transpose else (Ys @ W))
+        for _ in range(2):
+            out = torch.full((rows_out, width), float("nan"), device="cuda", dtype=dt)
+            svt.spmm_noalloc(P, y_dev, W_dev, out, transpose=transpose, precision=prec)
+            got = out.double().cpu().numpy()
+            assert np.linalg.norm(got - exact) / np.linalg.norm(exact) <= tol
