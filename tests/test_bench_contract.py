@@ -43,3 +43,29 @@ def test_reference_arm_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def test_traffic_is_reported_only_for_unchanged_sources(tmp_path, monkeypatch):
+    """The roofline's `traffic` comes from a committed ncu capture only while every source
+    file of the measured kernels is byte-identical to the one captured: a changed file
+    (here, one byte appended to the second of two) must make it null."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "paper_1704_05528_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "a.cu").write_bytes(b"kernel a\n")
+    (csrc / "b.cuh").write_bytes(b"kernel b\n")
+    h = hashlib.sha256(b"kernel a\n" + b"kernel b\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"step": {"sources": ["a.cu", "b.cuh"], "source_sha256_16": h, "bytes_per_launch": 1234},
+         "old": {"source": "a.cu", "source_sha256_16": hashlib.sha256(b"kernel a\n").hexdigest()[:16],
+                 "bytes_per_launch": 99}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("step") == 1234
+    assert bench.load_traffic("old") == 99          # a single-source record
+    assert bench.load_traffic("missing") is None
+    (csrc / "b.cuh").write_bytes(b"kernel b\n ")
+    assert bench.load_traffic("step") is None
+    assert bench.load_traffic("old") == 99
