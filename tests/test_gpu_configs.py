@@ -167,4 +167,3 @@ def test_config_ratings71567_mixed_through_the_heldout_minimum(env):
     got = _gpu(svt, torch, w, 60, "mixed")
     assert got.iters == ref.iters == 60
     _compare("ratings71567", w, ref, got, "mixed", sample=400_000)
-
