@@ -332,15 +332,17 @@ k_oa_finish(int r, const double* __restrict__ CS, double tol, int* __restrict__ 
     *status = (off <= tol * dg) ? 0 : 1;  // NaN counts as not converged
   }
   // rank of each eigenvalue: the number of eigenvalues placed before it (larger, or equal
-  // with a smaller index); a NaN ranks first and may share its slot, which the caller
-  // rejects as a non-finite eigenvalue
+  // with a smaller index; a NaN counts as larger than any number, so the order is total
+  // and the ranks distinct, and a NaN lands first, where the caller rejects it)
   double kt = 0.0;
   int rank = 0;
   if (t < r) {
     kt = key[t];
+    const bool nt = isnan(kt);
     for (int j = 0; j < r; ++j) {
       const double kj = key[j];
-      rank += (kj > kt) || (kj == kt && j < t);
+      const bool nj = isnan(kj);
+      rank += nj ? (!nt || j < t) : (!nt && (kj > kt || (kj == kt && j < t)));
     }
   }
   __syncthreads();
