@@ -306,43 +306,60 @@ k_oa_finish(int r, const double* __restrict__ CS, double tol, int* __restrict__ 
             const double* __restrict__ X, int64_t ldx, double* __restrict__ lam_out,
             double* __restrict__ Ub, int64_t ldu) {
   __shared__ double key[1024];
+  __shared__ unsigned long long okey[1024];
   __shared__ int idx[1024];
-  __shared__ double red_off[32], red_diag[32];
+  __shared__ unsigned long long red_off[32], red_diag[32];
   const int t = threadIdx.x;
   const int64_t ld = 2 * (int64_t)r;
+  // Comparisons run on the bit patterns in the integer pipes: binary64 runs at a small
+  // fraction of the rate, and this kernel is one block.  |v| orders as its bits without
+  // the sign (a NaN above infinity).
+  constexpr unsigned long long kAbs = 0x7fffffffffffffffull;
   if (status) {
-    double off = 0.0, dg = 0.0;
+    unsigned long long off = 0ull, dg = 0ull;
     for (int e = t; e < r * r; e += blockDim.x) {
       const int a = e / r, b = e - (e / r) * r;
-      const double v = fabs(CS[a * ld + r + b]);
-      if (a == b) dg = fmax(dg, v); else off = fmax(off, v);
+      const unsigned long long v = (unsigned long long)__double_as_longlong(CS[a * ld + r + b]) & kAbs;
+      if (a == b) dg = v > dg ? v : dg; else off = v > off ? v : off;
     }
     for (int o = 16; o > 0; o >>= 1) {
-      off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
-      dg = fmax(dg, __shfl_xor_sync(0xffffffffu, dg, o));
+      const unsigned long long xo = __shfl_xor_sync(0xffffffffu, off, o);
+      const unsigned long long xd = __shfl_xor_sync(0xffffffffu, dg, o);
+      off = xo > off ? xo : off;
+      dg = xd > dg ? xd : dg;
     }
     if ((t & 31) == 0) { red_off[t >> 5] = off; red_diag[t >> 5] = dg; }
   }
-  if (t < r) key[t] = CS[t * ld + r + t] / CS[t * ld + t];
+  if (t < r) {
+    const double lam = CS[t * ld + r + t] / CS[t * ld + t];
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(lam);
+    key[t] = lam;
+    // order-preserving key: larger value, larger key; a NaN above every number
+    okey[t] = (bits & kAbs) > 0x7ff0000000000000ull ? ~0ull
+              : (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull);
+  }
   idx[t] = t < r ? t : 0;
   __syncthreads();
   if (status && t == 0) {
-    double off = red_off[0], dg = red_diag[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { off = fmax(off, red_off[w]); dg = fmax(dg, red_diag[w]); }
-    *status = (off <= tol * dg) ? 0 : 1;  // NaN counts as not converged
+    unsigned long long off = red_off[0], dg = red_diag[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      off = red_off[w] > off ? red_off[w] : off;
+      dg = red_diag[w] > dg ? red_diag[w] : dg;
+    }
+    const double offd = __longlong_as_double((long long)off), dgd = __longlong_as_double((long long)dg);
+    *status = (offd <= tol * dgd) ? 0 : 1;  // NaN counts as not converged
   }
-  // rank of each eigenvalue: the number of eigenvalues placed before it (larger, or equal
-  // with a smaller index; a NaN counts as larger than any number, so the order is total
-  // and the ranks distinct, and a NaN lands first, where the caller rejects it)
+  // rank of each eigenvalue: the number of eigenvalues placed before it (larger key, or
+  // the same key with a smaller index); the order is total, so the ranks are distinct,
+  // and a NaN lands first, where the caller rejects it
   double kt = 0.0;
   int rank = 0;
   if (t < r) {
     kt = key[t];
-    const bool nt = isnan(kt);
+    const unsigned long long ot = okey[t];
     for (int j = 0; j < r; ++j) {
-      const double kj = key[j];
-      const bool nj = isnan(kj);
-      rank += nj ? (!nt || j < t) : (!nt && (kj > kt || (kj == kt && j < t)));
+      const unsigned long long oj = okey[j];
+      rank += (oj > ot) || (oj == ot && j < t);
     }
   }
   __syncthreads();
