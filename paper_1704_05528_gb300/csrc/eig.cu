@@ -893,12 +893,6 @@ svt_status eig_refine(int r, const double* G, int64_t ldg, double* lam, double* 
   return SVT_OK;
 }
 
-svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
-                   double* work, int refine_steps, cudaStream_t s) {
-  SVT_TRY(eig_start(r, G, ldg, work, s, nullptr));
-  return eig_refine(r, G, ldg, lam, Ub, ldu, work, refine_steps, s);
-}
-
 }  // namespace svt
 
 extern "C" unsigned svt_test_set_grid_wait_limit(unsigned polls) {

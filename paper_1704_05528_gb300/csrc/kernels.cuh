@@ -101,13 +101,9 @@ svt_status chol_inv(int w, const double* G, int64_t ldg, double* R, double* Rinv
 
 // eig.cu ----------------------------------------------------------------------
 size_t eig_scratch(int r);
-// Symmetric eigen-decomposition of the r x r binary64 matrix G (ldg): eigenvalues in
-// descending order (lam), eigenvectors as columns of Ub (r x r, ldu).  FP32 Jacobi
-// start, then binary64 refinement steps built from GEMMs.
-svt_status sym_eig(int r, const double* G, int64_t ldg, double* lam, double* Ub, int64_t ldu,
-                   double* work, int refine_steps, cudaStream_t s);
-// The two stages of sym_eig: binary32 Jacobi start (eigenvectors in work), then the
-// binary64 refinement and the sort.
+// Symmetric eigendecomposition of the r x r binary64 matrix G (ldg), in two stages: a
+// binary32 Jacobi start (eigenvectors in work), then the binary64 refinement, which leaves
+// the eigenvalues in descending order (lam) and the eigenvectors as columns of Ub.
 svt_status eig_start(int r, const double* G, int64_t ldg, double* work, cudaStream_t s,
                      int* sweeps_out, unsigned* status = nullptr);
 // Near-diagonal start for eig_refine (recycled bases): *status (device int) = 0 when the
